@@ -1,0 +1,232 @@
+"""CPU oracle for the Teukolsky Lax-Wendroff step (arXiv 1010.3816, Sec. 3).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It wraps the plain C
+implementation in ``tk_oracle.c`` (FP64, no FMA contraction, no fast-math),
+which shares no code with the CUDA path.
+
+The state layout is the paper's (Sec. 4): four planes ``qre, qim, pre, pim``,
+each ``[Ntheta][Nr]`` with the r* index fastest.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tk_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libtk_oracle.so")
+_lock = threading.Lock()
+_lib_handle = None
+
+NCOEF = 9
+COEF_NAMES = ("b", "c1R", "c1I", "c2R", "c2I", "c3R", "c3I", "c4", "c5")
+
+
+def build(force: bool = False) -> str:
+    """Compile ``tk_oracle.c`` into ``_build/libtk_oracle.so`` (with OpenMP if
+    the compiler supports it).  Returns the path of the shared library."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    base = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+            "-fPIC", "-shared", _SRC, "-o", _SO + ".tmp", "-lm"]
+    r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
+    if r.returncode != 0:
+        r = subprocess.run(base, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("oracle build failed:\n" + r.stderr)
+    os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+class Params(C.Structure):
+    _fields_ = [("M", C.c_double), ("a", C.c_double), ("s", C.c_int), ("m", C.c_int),
+                ("rs_min", C.c_double), ("drs", C.c_double), ("Nr", C.c_int), ("Ntheta", C.c_int),
+                ("dt", C.c_double), ("substeps", C.c_int), ("variable", C.c_int)]
+
+
+_dp = C.POINTER(C.c_double)
+
+
+def _lib():
+    global _lib_handle
+    with _lock:
+        if _lib_handle is None:
+            # TKO_SO names an alternative build of tk_oracle.c (used to check
+            # that the pins catch deliberately planted mistakes).
+            lib = C.CDLL(os.environ.get("TKO_SO") or build())
+            lib.tko_tortoise_x.restype = C.c_double
+            lib.tko_tortoise_x.argtypes = [C.c_double, C.c_double, C.c_double]
+            lib.tko_x_of_rstar.restype = C.c_double
+            lib.tko_x_of_rstar.argtypes = [C.c_double, C.c_double, C.c_double]
+            lib.tko_weight.restype = C.c_double
+            lib.tko_weight.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double]
+            lib.tko_parity.restype = C.c_int
+            lib.tko_parity.argtypes = [C.c_int, C.c_int]
+            lib.tko_coeffs_point.restype = None
+            lib.tko_coeffs_point.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int, C.c_int,
+                                             C.c_double, C.c_double, _dp]
+            lib.tko_angular_apply.restype = None
+            lib.tko_angular_apply.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp]
+            lib.tko_average.restype = None
+            lib.tko_average.argtypes = [_dp, _dp, C.c_int, C.c_int]
+            lib.tko_new.restype = C.c_void_p
+            lib.tko_new.argtypes = [C.POINTER(Params)]
+            lib.tko_free.restype = None
+            lib.tko_free.argtypes = [C.c_void_p]
+            lib.tko_get_coeffs.restype = None
+            lib.tko_get_coeffs.argtypes = [C.c_void_p, _dp, _dp]
+            lib.tko_set_initial.restype = None
+            lib.tko_set_initial.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
+            lib.tko_get_state.restype = None
+            lib.tko_get_state.argtypes = [C.c_void_p, _dp]
+            lib.tko_add_observer.restype = C.c_int
+            lib.tko_add_observer.argtypes = [C.c_void_p, C.c_double, C.c_double]
+            lib.tko_run.restype = None
+            lib.tko_run.argtypes = [C.c_void_p, C.c_int]
+            lib.tko_waveform.restype = C.c_int
+            lib.tko_waveform.argtypes = [C.c_void_p, C.c_int, _dp, _dp]
+            lib.tko_set_threads.restype = None
+            lib.tko_set_threads.argtypes = [C.c_int]
+            lib.tko_get_threads.restype = C.c_int
+            lib.tko_get_threads.argtypes = []
+            _lib_handle = lib
+        return _lib_handle
+
+
+def _ptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_dp)
+
+
+# --- point functions ---------------------------------------------------------
+def tortoise_x(M: float, a: float, x: float) -> float:
+    """r*(r) with x = r - r_+ (Kerr tortoise coordinate)."""
+    return _lib().tko_tortoise_x(M, a, x)
+
+
+def x_of_rstar(M: float, a: float, rstar: float) -> float:
+    """Inverse tortoise map: x = r - r_+ at a given r*."""
+    return _lib().tko_x_of_rstar(M, a, rstar)
+
+
+def horizons(M: float, a: float):
+    d = (M * M - a * a) ** 0.5
+    return M + d, M - d
+
+
+def weight(s: int, m: int, variable: int, theta: float) -> float:
+    return _lib().tko_weight(s, m, variable, theta)
+
+
+def parity(m: int, variable: int) -> int:
+    return _lib().tko_parity(m, variable)
+
+
+def coeffs_point(M, a, s, m, variable, x, theta) -> dict:
+    out = np.zeros(NCOEF)
+    _lib().tko_coeffs_point(M, a, s, m, variable, x, theta, _ptr(out))
+    return dict(zip(COEF_NAMES, out.tolist()))
+
+
+def angular_apply(s: int, m: int, variable: int, F: np.ndarray) -> np.ndarray:
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    out = np.zeros_like(F)
+    _lib().tko_angular_apply(s, m, variable, F.shape[0], _ptr(F), _ptr(out))
+    return out
+
+
+def average(q: np.ndarray) -> np.ndarray:
+    """The paper's kernel_average1 on one plane [Ntheta][Nr]; column 0 of the
+    result is left at zero."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    out = np.zeros_like(q)
+    _lib().tko_average(_ptr(q), _ptr(out), q.shape[1], q.shape[0])
+    return out
+
+
+def set_threads(n: int) -> None:
+    _lib().tko_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return _lib().tko_get_threads()
+
+
+# --- solver --------------------------------------------------------------------
+class Solver:
+    """One Teukolsky m-mode evolution on the CPU.
+
+    Parameters mirror the CUDA library's make_grid/precompute calls: the radial
+    grid is ``rs_min + a*drs`` for ``a < Nr``, the angular grid is
+    ``(b + 1/2) pi / Ntheta``; ``dt`` is the outer step, split into
+    ``substeps`` Lax-Wendroff steps; ``variable`` 0 evolves the literal
+    field, 1 the pole-regularised one.
+    """
+
+    def __init__(self, *, M=1.0, a=0.0, s=-2, m=2, rs_min, rs_max, Nr, Ntheta, dt,
+                 substeps=1, variable=1):
+        self.Nr, self.Ntheta = int(Nr), int(Ntheta)
+        drs = (rs_max - rs_min) / (Nr - 1)
+        self.params = Params(M, a, s, m, rs_min, drs, Nr, Ntheta, dt, substeps, variable)
+        self._h = _lib().tko_new(C.byref(self.params))
+        if not self._h:
+            raise ValueError("oracle rejected the parameters")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            _lib().tko_free(h)
+            self._h = None
+
+    @property
+    def drs(self) -> float:
+        return self.params.drs
+
+    def set_initial(self, phi_re, phi_im, pi_re=None, pi_im=None):
+        shp = (self.Ntheta, self.Nr)
+        pr = np.ascontiguousarray(phi_re, dtype=np.float64).reshape(shp)
+        pi = np.ascontiguousarray(phi_im, dtype=np.float64).reshape(shp)
+        if pi_re is None:
+            _lib().tko_set_initial(self._h, _ptr(pr), _ptr(pi), None, None)
+        else:
+            qr = np.ascontiguousarray(pi_re, dtype=np.float64).reshape(shp)
+            qi = np.ascontiguousarray(pi_im, dtype=np.float64).reshape(shp)
+            _lib().tko_set_initial(self._h, _ptr(pr), _ptr(pi), _ptr(qr), _ptr(qi))
+
+    def add_observer(self, rstar: float, theta: float) -> int:
+        k = _lib().tko_add_observer(self._h, rstar, theta)
+        if k < 0:
+            raise ValueError("observer outside the grid")
+        return k
+
+    def run(self, n: int) -> None:
+        _lib().tko_run(self._h, int(n))
+
+    def state(self) -> np.ndarray:
+        out = np.zeros((4, self.Ntheta, self.Nr))
+        _lib().tko_get_state(self._h, _ptr(out))
+        return out
+
+    def coeffs(self):
+        """(node, half) coefficient tables, each [NCOEF][Ntheta][Nr]; the half
+        table's column a >= 1 holds the values at r*_{a-1/2}."""
+        node = np.zeros((NCOEF, self.Ntheta, self.Nr))
+        half = np.zeros((NCOEF, self.Ntheta, self.Nr))
+        _lib().tko_get_coeffs(self._h, _ptr(node), _ptr(half))
+        return node, half
+
+    def waveform(self, obs_id: int) -> np.ndarray:
+        n = _lib().tko_waveform(self._h, obs_id, None, None)
+        if n < 0:
+            raise ValueError("bad observer id")
+        re = np.zeros(max(n, 1))
+        im = np.zeros(max(n, 1))
+        _lib().tko_waveform(self._h, obs_id, _ptr(re), _ptr(im))
+        return (re + 1j * im)[:n]
