@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 Teukolsky Lax-Wendroff solver.
+
+One benchmark step is one whole solve of the workload through the C ABI:
+Kerr coefficient precompute, initial data, every outer time step with its
+waveform samples, and the waveform read-out.  The default workload is the Kerr
+a = 0.9 M evolution on a 25601 x 64 grid for 38400 steps (t = 600 M).
+
+Printed: one JSON line with grid-point updates/s (value: inputs already in
+HBM; e2e: host buffers, copies inside the timed region), the roofline of the
+step kernel measured live with CUDA events, the clocks seen during the timed
+region, and the CPU oracle timed on a bounded sample on the host cores.
+
+``--impl reference`` times the CPU oracle instead (each step a bounded sample
+of the same workload) and prints the same line with ``"impl": "reference"``.
+
+Multi-GPU (torchrun): the solve does not shard in this build; each rank runs
+its own replica of the workload and ``value`` counts the updates of all ranks
+over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from inputs import KERR_25601x64, SCHWARZSCHILD_1601x32, initial_planes  # noqa: E402
+
+WORKLOADS = {"kerr": KERR_25601x64, "schwarzschild": SCHWARZSCHILD_1601x32}
+
+# FP64 work of the step kernel per grid-point update, counted from its source:
+# half node (Eq. lw1) 4 adds + 4 multiplies + 20 FMAs, node (Eq. lw2) 4 adds +
+# 24 FMAs; an FMA counts 2 flops.
+FP64_FLOP_PER_UPDATE = (4 + 4 + 2 * 20) + (4 + 2 * 24)          # = 100
+FP64_INSTR_PER_UPDATE = 28 + 28
+STATE_BYTES_PER_UPDATE = {0: 64, 1: 32}                         # read u^n, write u^{n+1}
+TABLE_BYTES_PER_UPDATE = {0: 21 * 8, 1: 21 * 4}                 # 11 + 10 table entries
+NUM_SMS = 152
+FP64_FMA_PER_CLK_PER_SM = 2        # measured: 1.19 TFLOP/s at 1995 MHz on 152 SMs
+FP32_FMA_PER_CLK_PER_SM = 128
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+                power.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _gpu_id(torch, dev: int) -> str:
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(dev)
+
+
+def cpu_baseline(w, sample_steps: int) -> dict:
+    """The CPU oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    oracle.build()
+    threads = oracle.get_threads()
+    sol = oracle.Solver(M=w.M, a=w.a, s=w.s, m=w.m, rs_min=w.rs_min, rs_max=w.rs_max, Nr=w.Nr,
+                        Ntheta=w.Ntheta, dt=w.dt, substeps=w.substeps, variable=w.variable)
+    for r, t in w.observers:
+        sol.add_observer(r, t)
+    re, im = initial_planes(w)
+    sol.set_initial(re, im)
+    t0 = time.perf_counter()
+    sol.run(sample_steps)
+    dt = time.perf_counter() - t0
+    ups = w.points * sample_steps * w.substeps / dt
+    return {"value": ups, "unit": "updates/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {sample_steps} of {w.steps} outer steps of {w.name} "
+                      f"(time stepping only, {threads} OpenMP threads, {os.cpu_count()} host cores)",
+            "seconds": dt}
+
+
+def run_reference(args, w):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    sample = args.ref_sample_steps
+    import oracle
+    oracle.build()
+    threads = oracle.get_threads()
+    sol = oracle.Solver(M=w.M, a=w.a, s=w.s, m=w.m, rs_min=w.rs_min, rs_max=w.rs_max, Nr=w.Nr,
+                        Ntheta=w.Ntheta, dt=w.dt, substeps=w.substeps, variable=w.variable)
+    for r, t in w.observers:
+        sol.add_observer(r, t)
+    re, im = initial_planes(w)
+    sol.set_initial(re, im)
+    for _ in range(args.warmup):
+        sol.run(sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sol.run(sample)
+    dt = time.perf_counter() - t0
+    ups = w.points * sample * w.substeps * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "grid-point updates/s", "value": ups, "unit": "updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(w, args, world),
+        "cpu_baseline": {"value": ups, "unit": "updates/s", "cores": threads, "kind": "oracle",
+                         "sample": f"each step: {sample} outer steps of {w.name} on the CPU oracle "
+                                   f"({threads} OpenMP threads, {os.cpu_count()} host cores)"},
+        "e2e": {"value": ups, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _config(w, args, world):
+    return {"workload": w.name, "a": w.a, "M": w.M, "s": w.s, "m": w.m, "Nr": w.Nr,
+            "Ntheta": w.Ntheta, "rstar": [w.rs_min, w.rs_max], "dt": w.dt,
+            "outer_steps": args.outer_steps or w.steps, "substeps": w.substeps,
+            "variable": "regularised" if w.variable else "literal",
+            "precision": "f32" if args.precision else "f64",
+            "observers": [list(o) for o in w.observers],
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2 (state 2x{:.0f} MB + tables {:.0f} MB)".format(
+                w.points * STATE_BYTES_PER_UPDATE[args.precision] / 1e6,
+                w.points * TABLE_BYTES_PER_UPDATE[args.precision] / 1e6)}
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tk", choices=["tk", "reference"])
+    ap.add_argument("--workload", default="kerr", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--outer-steps", type=int, default=0,
+                    help="outer steps per solve (default: the workload's); for profiling runs")
+    ap.add_argument("--cpu-sample-steps", type=int, default=150)
+    ap.add_argument("--ref-sample-steps", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import paper_1010_3816_gb300 as tk
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    tk.load_library()
+    n_outer = args.outer_steps or w.steps
+    updates = w.points * n_outer * w.substeps
+    launches_per_solve = 3 + n_outer * w.substeps + len(w.observers)
+
+    stream = torch.cuda.current_stream()
+    solver = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
+                       substeps=w.substeps, variable=w.variable, precision=args.precision,
+                       stream=stream.cuda_stream)
+    re, im = initial_planes(w)
+    d_re = torch.from_numpy(re).cuda()
+    d_im = torch.from_numpy(im).cuda()
+    obs_out = [(torch.empty(n_outer, dtype=torch.float64, device="cuda"),
+                torch.empty(n_outer, dtype=torch.float64, device="cuda")) for _ in w.observers]
+    solver.precompute(w.a, w.M, w.s, w.m)
+    solver.set_initial(d_re, d_im)
+    obs_ids = [solver.add_observer(r, t) for r, t in w.observers]
+
+    ev_step = []
+
+    def solve_device(record: bool):
+        tk.tk_precompute_coeffs(solver.h, w.a, w.M, w.s, w.m)
+        tk.tk_set_initial_data(solver.h, d_re, d_im)
+        if record:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        tk.tk_step(solver.h, n_outer)
+        if record:
+            e1.record(stream)
+            ev_step.append((e0, e1))
+        for k, (a, b) in zip(obs_ids, obs_out):
+            tk.tk_extract(solver.h, k, a, b)
+
+    for _ in range(args.warmup):
+        solve_device(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(_gpu_id(torch, local))
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        solve_device(True)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * updates * args.steps / (ms * 1e-3)
+    step_ms = [a.elapsed_time(b) for a, b in ev_step]
+    kern_s = statistics.mean(step_ms) * 1e-3 / (n_outer * w.substeps)   # per launch
+    pts = w.points
+    f_clk = (clk.get("sm_mhz") or 2070.0) * 1e6
+    if args.precision == 0:
+        achieved = FP64_FLOP_PER_UPDATE * pts / kern_s / 1e12
+        peak = NUM_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * f_clk / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "lw_step_kernel<double>",
+                "peak_source": "152 SMs x 2 DFMA/clk (measured) x 2 flop x median SM clock "
+                               f"{f_clk / 1e6:.0f} MHz",
+                "flop_per_update": FP64_FLOP_PER_UPDATE,
+                "fp64_issue_frac": FP64_INSTR_PER_UPDATE * pts / kern_s /
+                (NUM_SMS * FP64_FMA_PER_CLK_PER_SM * f_clk),
+                "launch_us": kern_s * 1e6}
+    else:
+        achieved = STATE_BYTES_PER_UPDATE[1] * pts / kern_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": 6794.1, "unit": "GB/s",
+                "frac": achieved / 6794.1, "traffic": None, "kernel": "lw_step_kernel<float>",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "launch_us": kern_s * 1e6}
+    sb = STATE_BYTES_PER_UPDATE[args.precision] * pts / kern_s / 1e9
+    tb = TABLE_BYTES_PER_UPDATE[args.precision] * pts / kern_s / 1e9
+    roof_hbm = {"bound": "hbm", "achieved": sb, "peak": 6794.1, "unit": "GB/s",
+                "frac": sb / 6794.1, "state_bytes_per_update": STATE_BYTES_PER_UPDATE[args.precision],
+                "table_gbs": tb, "table_bytes_per_update": TABLE_BYTES_PER_UPDATE[args.precision],
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+    # end to end through the public API: host input planes (pinned), host waveform read-back
+    e2e = None
+    if not args.no_e2e:
+        h_re = torch.from_numpy(re).pin_memory()
+        h_im = torch.from_numpy(im).pin_memory()
+        h_out = [(np.zeros(n_outer), np.zeros(n_outer)) for _ in w.observers]
+        h2d = 2 * re.nbytes
+        d2h = sum(2 * 8 * n_outer for _ in w.observers)
+
+        def solve_host():
+            tk.tk_precompute_coeffs(solver.h, w.a, w.M, w.s, w.m)
+            tk.tk_set_initial_data(solver.h, h_re.numpy(), h_im.numpy())
+            tk.tk_step(solver.h, n_outer)
+            for k, (a, b) in zip(obs_ids, h_out):
+                tk.tk_extract(solver.h, k, a, b)
+
+        solve_host()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            solve_host()
+        torch.cuda.synchronize()
+        es = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([es], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            es = float(t.item())
+        e2e = {"value": world * updates * args.steps / es, "unit": "updates/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": 1e3 * es / args.steps}
+
+    solver.check_finite()
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(w, args.cpu_sample_steps)
+        line = {
+            "metric": "grid-point updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision else "f64", "data": "synthetic",
+            "config": _config(w, args, world), "roofline": roof, "roofline_hbm": roof_hbm,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": launches_per_solve * args.steps,
+        }
+        print(json.dumps(line))
+    solver.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,153 @@
+/*
+ * tk.h -- C ABI of a GB300 (sm_103a) solver for the homogeneous (2+1)D
+ * Teukolsky equation, time-stepped with the two-step 2nd-order Lax-Wendroff
+ * scheme of arXiv 1010.3816 (Choudhary, Navada, Ginjupalli, Khanna), Sec. 3.
+ *
+ * One solver evolves one azimuthal mode m of a spin-weight-s field on a Kerr
+ * black hole of mass M and spin a, on a uniform grid in the tortoise
+ * coordinate r* and the polar angle theta.  The state is the solution vector
+ * of Eq. (lw1)/(lw2), u = {Phi_R, Phi_I, Pi_R, Pi_I}, with Pi the momentum of
+ * Sec. 3.2.  All arithmetic of the path runs in CUDA kernels; the host code
+ * behind this header only validates arguments, allocates device memory and
+ * enqueues work.
+ *
+ * Conventions shared by every entry point
+ *   - Field planes: four planes Phi_R, Phi_I, Pi_R, Pi_I, each laid out as
+ *     plane[j * Nr + i] (theta row j, r* index i fastest), the layout of the
+ *     paper's kernels (Sec. 4: idx(b,a) = N*b + a).  "planes4" means the four
+ *     planes back to back in that order (4 * Ntheta * Nr doubles).
+ *   - Grid: r*_i = rstar_min + i * dr*, dr* = (rstar_max - rstar_min)/(Nr-1);
+ *     theta_j = (j + 1/2) * dtheta, dtheta = pi/Ntheta (cell-centred, no
+ *     node on a pole).
+ *   - Pointers are plain host or device pointers as the on_device flag says;
+ *     device pointers must be in this GPU's memory.  The caller owns every
+ *     buffer it passes; the solver copies inputs and never keeps a caller
+ *     pointer.  Host buffers may be pageable or pinned.
+ *   - Every call is asynchronous on the CUDA stream given to tk_make_grid,
+ *     except calls that return data to host memory, which synchronize that
+ *     stream before returning.
+ *   - Errors: every call returns a tk_status.  No call aborts or throws.  On
+ *     error the solver keeps its previous state and tk_last_error() returns a
+ *     one-line message.  A CUDA error is returned as TK_ERR_CUDA.
+ *   - Calls must come in the order make_grid -> precompute_coeffs ->
+ *     set_initial_data -> (add_observer | step | extract | get_state)*;
+ *     out-of-order calls return TK_ERR_STATE.
+ *   - A solver may be used by one host thread at a time.
+ */
+#ifndef TK_H
+#define TK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tk_solver tk_solver;
+
+typedef enum {
+    TK_OK = 0,
+    TK_ERR_ARG = 1,       /* invalid argument (null pointer, size, range)        */
+    TK_ERR_STATE = 2,     /* call out of order                                   */
+    TK_ERR_CUDA = 3,      /* a CUDA runtime call failed                          */
+    TK_ERR_OOM = 4,       /* device allocation failed                            */
+    TK_ERR_UNSTABLE = 5,  /* non-finite values detected in the state             */
+    TK_ERR_INTERNAL = 6   /* device-side consistency check failed                */
+} tk_status;
+
+/* Angular variable evolved by the solver. */
+enum {
+    TK_VAR_LITERAL = 0,     /* Phi itself; ghost parity (-1)^|m| (Sec. 3.2)      */
+    TK_VAR_REGULARISED = 1  /* Phi^ = Phi / w(theta), w = (1-cos)^{|m+s|/2}
+                               (1+cos)^{|m-s|/2}; ghost parity +1               */
+};
+
+/* Arithmetic of the time step. */
+enum {
+    TK_PREC_F64 = 0,        /* FP64 planes, tables and arithmetic                */
+    TK_PREC_F32 = 1         /* FP32 planes, tables and stencil arithmetic; FP64
+                               coefficient precompute and waveform samples      */
+};
+
+/* Create a solver for an Nr x Ntheta grid (Sec. 3.2).
+ *   rstar_min < rstar_max   radial extent (tortoise coordinate, units of M)
+ *   Nr >= 3, 2 <= Ntheta <= 128
+ *   dt > 0                  outer time step: one waveform sample per outer step
+ *   substeps >= 1           Lax-Wendroff steps per outer step (each dt/substeps);
+ *                           0 means 1
+ *   angular_variable        TK_VAR_LITERAL or TK_VAR_REGULARISED
+ *   precision               TK_PREC_F64 or TK_PREC_F32
+ *   cuda_stream             cudaStream_t to run on (NULL: the legacy default stream)
+ * Allocates the device state (two time levels) and nothing else yet.
+ * Returns TK_ERR_ARG on a bad size, TK_ERR_OOM if allocation fails. */
+tk_status tk_make_grid(tk_solver **out, double rstar_min, double rstar_max, int Nr, int Ntheta,
+                       double dt, int substeps, int angular_variable, int precision,
+                       void *cuda_stream);
+
+/* Kerr coefficient precompute for black-hole spin a and mass M (|a| < M),
+ * spin weight s and azimuthal mode m (Eq. 1, Eq. 2).  Runs in FP64 on the
+ * device: inverts the tortoise map r*(r) at every node and half node, forms
+ * the coefficients of the first-order system derived from Eq. 1 (matrices D
+ * and S of Eqs. lw1/lw2), folds in dt, dr*, dtheta and the angular boundary
+ * conditions of Sec. 3.2, and stores them as the step kernel's tables.  May
+ * be called again to change (a, M, s, m); the state must then be set again.
+ * Returns TK_ERR_ARG unless M > 0 and |a| < M. */
+tk_status tk_precompute_coeffs(tk_solver *S, double a, double M, int s, int m);
+
+/* Initial data (Sec. 3.2).  phi_re, phi_im: planes [Ntheta][Nr] of the evolved
+ * field (Phi, or Phi^ = Phi/w in the regularised variable).  pi_re, pi_im: the
+ * momentum planes, or both NULL for zero time derivative, Pi = b d_{r*} Phi
+ * with the centred difference at interior nodes.  Both fields are set to zero
+ * on the two radial edges (Sec. 3.2).  on_device: 1 if the pointers are device
+ * pointers, 0 if host.  Resets the step counter and every observer. */
+tk_status tk_set_initial_data(tk_solver *S, const double *phi_re, const double *phi_im,
+                              const double *pi_re, const double *pi_im, int on_device);
+
+/* Register a waveform observer at (rstar_obs, theta_obs); writes its id.  The
+ * sample after every outer step is the bilinear interpolant in (r*, theta) of
+ * the physical field Phi = w Phi^ (w = 1 for the literal variable).  The point
+ * must lie in [r*_0, r*_{Nr-1}] x [theta_0, theta_{Ntheta-1}] (TK_ERR_ARG
+ * otherwise).  At most 16 observers.  Observers are added after
+ * tk_set_initial_data and before the first tk_step (TK_ERR_STATE otherwise);
+ * they persist across later tk_set_initial_data calls. */
+tk_status tk_add_observer(tk_solver *S, double rstar_obs, double theta_obs, int *obs_id);
+
+/* Advance n >= 0 outer steps (Eqs. lw1 then lw2, with the theta-pole ghosts
+ * and radial-edge zeros folded in), appending one sample per observer per
+ * outer step.  Asynchronous. */
+tk_status tk_step(tk_solver *S, int n);
+
+/* Waveform of observer obs_id: copies the first min(count, capacity) samples
+ * into re[], im[] (device pointers if on_device) and writes the total sample
+ * count to *count.  re/im may be NULL with capacity 0 to query the count. */
+tk_status tk_extract(tk_solver *S, int obs_id, double *re, double *im, int capacity, int *count,
+                     int on_device);
+
+/* Current state as planes4 (4 * Ntheta * Nr doubles), host or device. */
+tk_status tk_get_state(tk_solver *S, double *planes4, int on_device);
+
+/* Overwrite the state from planes4 (checkpoint restore); keeps observers and
+ * the step counter. */
+tk_status tk_set_state(tk_solver *S, const double *planes4, int on_device);
+
+/* Outer steps taken since the initial data. */
+tk_status tk_steps_done(const tk_solver *S, int64_t *steps);
+
+/* Check that every value of the state is finite; returns TK_ERR_UNSTABLE if
+ * not.  Synchronizes the stream. */
+tk_status tk_check_finite(tk_solver *S);
+
+/* Wait for all work queued by this solver. */
+tk_status tk_synchronize(tk_solver *S);
+
+/* One-line description of the last error on this solver (never NULL). */
+const char *tk_last_error(const tk_solver *S);
+
+/* Release every device buffer of the solver.  NULL is ignored. */
+void tk_destroy(tk_solver *S);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TK_H */

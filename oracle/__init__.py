@@ -74,6 +74,10 @@ def _lib():
                                              C.c_double, C.c_double, _dp]
             lib.tko_angular_apply.restype = None
             lib.tko_angular_apply.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp]
+            lib.tko_angular_apply_many.restype = None
+            lib.tko_angular_apply_many.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _dp, _dp]
+            lib.tko_regular_stencil.restype = None
+            lib.tko_regular_stencil.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp]
             lib.tko_average.restype = None
             lib.tko_average.argtypes = [_dp, _dp, C.c_int, C.c_int]
             lib.tko_new.restype = C.c_void_p
@@ -140,6 +144,23 @@ def angular_apply(s: int, m: int, variable: int, F: np.ndarray) -> np.ndarray:
     out = np.zeros_like(F)
     _lib().tko_angular_apply(s, m, variable, F.shape[0], _ptr(F), _ptr(out))
     return out
+
+
+def angular_matrix(s: int, m: int, variable: int, Ntheta: int) -> np.ndarray:
+    """Matrix of the discrete angular operator, column k = operator applied to
+    the k-th unit vector."""
+    eye = np.ascontiguousarray(np.eye(Ntheta))
+    out = np.zeros_like(eye)
+    _lib().tko_angular_apply_many(s, m, variable, Ntheta, Ntheta, _ptr(eye), _ptr(out))
+    return out.T.copy()
+
+
+def regular_stencil(s: int, m: int, Ntheta: int):
+    """(Ap, Am): the self-adjoint angular stencil of the regularised variable."""
+    Ap = np.zeros(Ntheta)
+    Am = np.zeros(Ntheta)
+    _lib().tko_regular_stencil(s, m, Ntheta, _ptr(Ap), _ptr(Am))
+    return Ap, Am
 
 
 def average(q: np.ndarray) -> np.ndarray:

@@ -20,8 +20,10 @@
  *   - The two-step Lax-Wendroff update, Eq. (lw1) then Eq. (lw2), with the
  *     averaging stage exactly as the paper's kernel_average1 (Sec. 4).
  *   - 2nd-order centred angular differences (Sec. 3.2) on a cell-centred
- *     theta grid, with the angular boundary conditions of Sec. 3.2 imposed by
- *     ghost parity, and Phi = Pi = 0 on both radial edges.
+ *     theta grid: for the literal field the paper's boundary conditions of
+ *     Sec. 3.2 are imposed by ghost parity; for the pole-regularised field
+ *     the operator is differenced in self-adjoint form, regular at the poles.
+ *     Phi = Pi = 0 on both radial edges.
  *   - The tortoise coordinate r*(r) of Kerr (not printed in the paper) and
  *     its inverse; a pole-regularised angular variable Phi = w(theta) Phi^;
  *     initial momentum for zero time derivative; bilinear waveform
@@ -214,21 +216,75 @@ int tko_parity(int m, int variable)
     return (abs(m) % 2 == 0) ? 1 : -1;
 }
 
-/* out_j = (F_{j+1} - 2F_j + F_{j-1})/dth^2 + g_j (F_{j+1} - F_{j-1})/(2 dth) + V_j F_j
- * on theta_j = (j + 1/2) pi / Ntheta, ghosts F_{-1} = p F_0, F_{N} = p F_{N-1}.
- * This is exactly the angular part of S divided by c4. */
-void tko_angular_apply(int s, int m, int variable, int Ntheta, const double *F, double *out)
+/* The regularised angular operator written in self-adjoint form.  With
+ * Phi = w F and (L_theta + V_theta) w = -lambda0 w,
+ *   (L_theta + V_theta)(w F) = w [ (P F')' / P - lambda0 F ],  P = sin(theta) w^2,
+ * since P'/P = cot(theta) + 2 w'/w.  Its 2nd-order centred difference on
+ * cell j = [j dth, (j+1) dth] is
+ *   [ P_{j+1} (F_{j+1} - F_j) - P_j (F_j - F_{j-1}) ] / (Q_j dth^2),
+ * with P_f = P(f dth) at the cell faces (P_0 = P_N = 0: no ghost is needed,
+ * the field is regular at the poles) and Q_j the mean of P over cell j.
+ * The matrix is symmetric in the Q-weighted inner product, so its
+ * eigenvalues are real.  Returns Ap_j = P_{j+1}/(Q_j dth^2) and
+ * Am_j = P_j/(Q_j dth^2).  Q_j uses composite Simpson with 20000 panels. */
+static double sl_weight(int s, int m, double th)
+{
+    double w = tko_weight(s, m, 1, th);
+    return sin(th) * w * w;
+}
+
+void tko_regular_stencil(int s, int m, int Ntheta, double *Ap, double *Am)
+{
+    double dth = M_PI / Ntheta;
+    const int n = 20000;
+    for (int j = 0; j < Ntheta; ++j) {
+        double lo = j * dth, h = dth / n, acc = 0.0;
+        for (int k = 0; k <= n; ++k) {
+            double wk = (k == 0 || k == n) ? 1.0 : ((k % 2) ? 4.0 : 2.0);
+            acc += wk * sl_weight(s, m, lo + k * h);
+        }
+        double Q = acc * h / 3.0 / dth;
+        double Plo = (j == 0) ? 0.0 : sl_weight(s, m, j * dth);
+        double Phi = (j == Ntheta - 1) ? 0.0 : sl_weight(s, m, (j + 1) * dth);
+        Ap[j] = Phi / (Q * dth * dth);
+        Am[j] = Plo / (Q * dth * dth);
+    }
+}
+
+/* The discrete angular operator divided by c4 (the angular part of S):
+ *   literal:     out_j = (F_{j+1} - 2F_j + F_{j-1})/dth^2 + cot(theta_j) (F_{j+1} - F_{j-1})/(2 dth)
+ *                        + V_theta(theta_j) F_j,  ghosts F_{-1} = p F_0, F_{N} = p F_{N-1};
+ *   regularised: out_j = Ap_j (F_{j+1} - F_j) - Am_j (F_j - F_{j-1}) - lambda0 F_j. */
+void tko_angular_apply_many(int s, int m, int variable, int Ntheta, int nvec, const double *F,
+                            double *out)
 {
     double dth = M_PI / Ntheta;
     int p = tko_parity(m, variable);
-    for (int j = 0; j < Ntheta; ++j) {
-        double th = (j + 0.5) * dth;
-        double g, V;
-        angular_parts(s, m, variable, th, &g, &V);
-        double Fm = (j == 0) ? p * F[0] : F[j - 1];
-        double Fp = (j == Ntheta - 1) ? p * F[Ntheta - 1] : F[j + 1];
-        out[j] = (Fp - 2.0 * F[j] + Fm) / (dth * dth) + g * (Fp - Fm) / (2.0 * dth) + V * F[j];
+    double *Ap = (double *)calloc(Ntheta, sizeof(double));
+    double *Am = (double *)calloc(Ntheta, sizeof(double));
+    if (variable != 0) tko_regular_stencil(s, m, Ntheta, Ap, Am);
+    for (int v = 0; v < nvec; ++v) {
+        const double *f = F + (size_t)v * Ntheta;
+        double *o = out + (size_t)v * Ntheta;
+        for (int j = 0; j < Ntheta; ++j) {
+            double th = (j + 0.5) * dth;
+            double g, V;
+            angular_parts(s, m, variable, th, &g, &V);
+            double Fm = (j == 0) ? p * f[0] : f[j - 1];
+            double Fp = (j == Ntheta - 1) ? p * f[Ntheta - 1] : f[j + 1];
+            if (variable == 0)
+                o[j] = (Fp - 2.0 * f[j] + Fm) / (dth * dth) + g * (Fp - Fm) / (2.0 * dth) + V * f[j];
+            else
+                o[j] = Ap[j] * (Fp - f[j]) - Am[j] * (f[j] - Fm) + V * f[j];
+        }
     }
+    free(Ap);
+    free(Am);
+}
+
+void tko_angular_apply(int s, int m, int variable, int Ntheta, const double *F, double *out)
+{
+    tko_angular_apply_many(s, m, variable, Ntheta, 1, F, out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -262,6 +318,7 @@ typedef struct {
     double *q_h[4];     /* half-step planes, index a >= 1 is node a-1/2       */
     double *rhs[4];     /* bracketed right-hand sides                         */
     double *avg[4];     /* averaged state used inside S                       */
+    double *ang_p, *ang_m; /* regularised angular stencil Ap_j, Am_j          */
     tko_observer obs[16];
     int nobs;
     long long steps_done;
@@ -308,6 +365,9 @@ tko_state *tko_new(const tko_params *p)
     }
     free(xn);
     free(xh);
+    S->ang_p = (double *)calloc(Nth, sizeof(double));
+    S->ang_m = (double *)calloc(Nth, sizeof(double));
+    if (p->variable != 0) tko_regular_stencil(p->s, p->m, Nth, S->ang_p, S->ang_m);
     return S;
 }
 
@@ -316,6 +376,8 @@ void tko_free(tko_state *S)
     if (!S) return;
     free(S->coef_node);
     free(S->coef_half);
+    free(S->ang_p);
+    free(S->ang_m);
     for (int k = 0; k < 4; ++k) { free(S->q[k]); free(S->q_h[k]); free(S->rhs[k]); free(S->avg[k]); }
     for (int o = 0; o < S->nobs; ++o) free(S->obs[o].wave);
     free(S);
@@ -370,9 +432,8 @@ void tko_get_state(const tko_state *S, double *out4)
 /*     (1/dr*) D (u_right - u_left) - S(u_avg)                               */
 /* at one point, given the averaged state at theta rows b-1, b, b+1.         */
 /* ------------------------------------------------------------------------ */
-static void bracket(const double *cf, double drs, double dth,
-                    const double du[4], const double um[4], const double u0[4], const double up[4],
-                    double out[4])
+static void bracket(const double *cf, double drs, const double du[4], const double u0[4],
+                    const double ang[2], double out[4])
 {
     double bb = cf[K_B];
     /* D as a real 4x4 matrix on (PhiR, PhiI, PiR, PiI): complex blocks
@@ -383,24 +444,32 @@ static void bracket(const double *cf, double drs, double dth,
         { -cf[K_C1R], cf[K_C1I], -bb, 0.0 },
         { -cf[K_C1I], -cf[K_C1R], 0.0, -bb },
     };
-    /* S(u): Phi rows = Pi; Pi rows = c2 Pi + c3 Phi + c4 d_thth Phi + c5 d_th Phi */
-    double dthth_R = (up[0] - 2.0 * u0[0] + um[0]) / (dth * dth);
-    double dthth_I = (up[1] - 2.0 * u0[1] + um[1]) / (dth * dth);
-    double dth_R = (up[0] - um[0]) / (2.0 * dth);
-    double dth_I = (up[1] - um[1]) / (2.0 * dth);
+    /* S(u): Phi rows = Pi; Pi rows = c2 Pi + c3 Phi + (angular term) */
     double Svec[4];
     Svec[0] = u0[2];
     Svec[1] = u0[3];
-    Svec[2] = cf[K_C2R] * u0[2] - cf[K_C2I] * u0[3]
-            + cf[K_C3R] * u0[0] - cf[K_C3I] * u0[1]
-            + cf[K_C4] * dthth_R + cf[K_C5] * dth_R;
-    Svec[3] = cf[K_C2R] * u0[3] + cf[K_C2I] * u0[2]
-            + cf[K_C3R] * u0[1] + cf[K_C3I] * u0[0]
-            + cf[K_C4] * dthth_I + cf[K_C5] * dth_I;
+    Svec[2] = cf[K_C2R] * u0[2] - cf[K_C2I] * u0[3] + cf[K_C3R] * u0[0] - cf[K_C3I] * u0[1] + ang[0];
+    Svec[3] = cf[K_C2R] * u0[3] + cf[K_C2I] * u0[2] + cf[K_C3R] * u0[1] + cf[K_C3I] * u0[0] + ang[1];
     for (int k = 0; k < 4; ++k) {
         double Dd = 0.0;
         for (int l = 0; l < 4; ++l) Dd += D[k][l] * du[l];
         out[k] = Dd / drs - Svec[k];
+    }
+}
+
+/* Angular part of S acting on the averaged Phi at theta row b (Sec. 3.2,
+ * 2nd-order centred differences):
+ *   literal:     c4 (F_{b+1} - 2F_b + F_{b-1})/dth^2 + c5 (F_{b+1} - F_{b-1})/(2 dth)
+ *   regularised: c4 [Ap_b (F_{b+1} - F_b) - Am_b (F_b - F_{b-1})]           */
+static void angular_term(const tko_state *S, const double *cf, int b, double dth,
+                         const double um[4], const double u0[4], const double up[4], double ang[2])
+{
+    for (int k = 0; k < 2; ++k) {
+        if (S->p.variable == 0)
+            ang[k] = cf[K_C4] * (up[k] - 2.0 * u0[k] + um[k]) / (dth * dth)
+                   + cf[K_C5] * (up[k] - um[k]) / (2.0 * dth);
+        else
+            ang[k] = cf[K_C4] * (S->ang_p[b] * (up[k] - u0[k]) - S->ang_m[b] * (u0[k] - um[k]));
     }
 }
 
@@ -429,14 +498,15 @@ static void lw_step(tko_state *S, double dt)
     /* Eq. (lw1), bracket at the half nodes a-1/2 (index a, 1 <= a < Nr). */
 #pragma omp parallel for schedule(static)
     for (int b = 0; b < Nth; ++b) {
-        double cf[NCOEF], du[4], um[4], u0[4], up[4], br[4];
+        double cf[NCOEF], du[4], um[4], u0[4], up[4], br[4], ang[2];
         for (int a = 1; a < Nr; ++a) {
             for (int k = 0; k < NCOEF; ++k) cf[k] = S->coef_half[k * plane + IDX(b, a)];
             for (int k = 0; k < 4; ++k) du[k] = S->q[k][IDX(b, a)] - S->q[k][IDX(b, a - 1)];
             avg_row(S->avg, Nr, Nth, parity, b - 1, a, um);
             avg_row(S->avg, Nr, Nth, parity, b, a, u0);
             avg_row(S->avg, Nr, Nth, parity, b + 1, a, up);
-            bracket(cf, drs, dth, du, um, u0, up, br);
+            angular_term(S, cf, b, dth, um, u0, up, ang);
+            bracket(cf, drs, du, u0, ang, br);
             for (int k = 0; k < 4; ++k) S->rhs[k][IDX(b, a)] = br[k];
         }
     }
@@ -456,14 +526,15 @@ static void lw_step(tko_state *S, double dt)
     /* Eq. (lw2), bracket at the interior nodes. */
 #pragma omp parallel for schedule(static)
     for (int b = 0; b < Nth; ++b) {
-        double cf[NCOEF], du[4], um[4], u0[4], up[4], br[4];
+        double cf[NCOEF], du[4], um[4], u0[4], up[4], br[4], ang[2];
         for (int a = 1; a < Nr - 1; ++a) {
             for (int k = 0; k < NCOEF; ++k) cf[k] = S->coef_node[k * plane + IDX(b, a)];
             for (int k = 0; k < 4; ++k) du[k] = S->q_h[k][IDX(b, a + 1)] - S->q_h[k][IDX(b, a)];
             avg_row(S->avg, Nr, Nth, parity, b - 1, a, um);
             avg_row(S->avg, Nr, Nth, parity, b, a, u0);
             avg_row(S->avg, Nr, Nth, parity, b + 1, a, up);
-            bracket(cf, drs, dth, du, um, u0, up, br);
+            angular_term(S, cf, b, dth, um, u0, up, ang);
+            bracket(cf, drs, du, u0, ang, br);
             for (int k = 0; k < 4; ++k) S->rhs[k][IDX(b, a)] = br[k];
         }
     }

@@ -1,0 +1,263 @@
+"""Python binding of libtk, the GB300 (sm_103a) Teukolsky Lax-Wendroff solver.
+
+The functions below carry the names of the C ABI in ``include/tk.h`` and only
+marshal arguments: every step of the computation runs in the library's CUDA
+kernels.  Arrays are numpy arrays (host memory, ``on_device=0``) or CUDA
+torch tensors (device memory, ``on_device=1``); PyTorch supplies device memory
+and the CUDA stream.  If ``libtk.so`` has not been built the import of the
+library fails loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtk.so")
+
+TK_OK, TK_ERR_ARG, TK_ERR_STATE, TK_ERR_CUDA, TK_ERR_OOM, TK_ERR_UNSTABLE, TK_ERR_INTERNAL = range(7)
+TK_VAR_LITERAL, TK_VAR_REGULARISED = 0, 1
+TK_PREC_F64, TK_PREC_F32 = 0, 1
+_STATUS = {0: "TK_OK", 1: "TK_ERR_ARG", 2: "TK_ERR_STATE", 3: "TK_ERR_CUDA", 4: "TK_ERR_OOM",
+           5: "TK_ERR_UNSTABLE", 6: "TK_ERR_INTERNAL"}
+
+# every symbol declared in include/tk.h
+EXPORTS = ("tk_make_grid", "tk_precompute_coeffs", "tk_set_initial_data", "tk_add_observer",
+           "tk_step", "tk_extract", "tk_get_state", "tk_set_state", "tk_steps_done",
+           "tk_check_finite", "tk_synchronize", "tk_last_error", "tk_destroy")
+
+
+class TkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib_handle = None
+_vp, _dp, _ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libtk.so and declare its signatures (raises if it is missing)."""
+    global _lib_handle
+    with _lock:
+        if _lib_handle is not None:
+            return _lib_handle
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = C.CDLL(path)
+        sig = {
+            "tk_make_grid": (C.c_int, [C.POINTER(_vp), C.c_double, C.c_double, C.c_int, C.c_int,
+                                       C.c_double, C.c_int, C.c_int, C.c_int, _vp]),
+            "tk_precompute_coeffs": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int, C.c_int]),
+            "tk_set_initial_data": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int]),
+            "tk_add_observer": (C.c_int, [_vp, C.c_double, C.c_double, _ip]),
+            "tk_step": (C.c_int, [_vp, C.c_int]),
+            "tk_extract": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, _ip, C.c_int]),
+            "tk_get_state": (C.c_int, [_vp, _vp, C.c_int]),
+            "tk_set_state": (C.c_int, [_vp, _vp, C.c_int]),
+            "tk_steps_done": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
+            "tk_check_finite": (C.c_int, [_vp]),
+            "tk_synchronize": (C.c_int, [_vp]),
+            "tk_last_error": (C.c_char_p, [_vp]),
+            "tk_destroy": (None, [_vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib_handle = lib
+        return lib
+
+
+def _check(h, status: int):
+    if status != TK_OK:
+        raise TkError(status, load_library().tk_last_error(h).decode())
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+def _arg(x, n: Optional[int] = None):
+    """(pointer, on_device, keepalive) for a numpy array or a CUDA torch tensor."""
+    if x is None:
+        return None, None, None
+    if isinstance(x, np.ndarray):
+        a = np.ascontiguousarray(x, dtype=np.float64)
+        if n is not None and a.size < n:
+            raise ValueError(f"array has {a.size} elements, need {n}")
+        return a.ctypes.data, 0, a
+    import torch
+    if isinstance(x, torch.Tensor):
+        if not x.is_cuda or x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("device arrays must be contiguous float64 CUDA tensors")
+        if n is not None and x.numel() < n:
+            raise ValueError(f"tensor has {x.numel()} elements, need {n}")
+        return x.data_ptr(), 1, x
+    raise TypeError(f"unsupported array type {type(x)}")
+
+
+# --- the C ABI, one function per entry point --------------------------------------
+def tk_make_grid(rstar_min: float, rstar_max: float, Nr: int, Ntheta: int, dt: float,
+                 substeps: int = 1, angular_variable: int = TK_VAR_REGULARISED,
+                 precision: int = TK_PREC_F64, stream=None):
+    lib = load_library()
+    h = _vp()
+    st = _current_stream() if stream is None else stream
+    status = lib.tk_make_grid(C.byref(h), rstar_min, rstar_max, Nr, Ntheta, dt, substeps,
+                              angular_variable, precision, _vp(st))
+    _check(None, status)
+    return h
+
+
+def tk_precompute_coeffs(h, a: float, M: float, s: int, m: int) -> None:
+    _check(h, load_library().tk_precompute_coeffs(h, a, M, s, m))
+
+
+def tk_set_initial_data(h, phi_re, phi_im, pi_re=None, pi_im=None) -> None:
+    p = [_arg(x) for x in (phi_re, phi_im, pi_re, pi_im)]
+    dev = {q[1] for q in p if q[1] is not None}
+    if len(dev) != 1:
+        raise ValueError("all arrays must be on the host or all on the device")
+    _check(h, load_library().tk_set_initial_data(h, p[0][0], p[1][0], p[2][0], p[3][0], dev.pop()))
+
+
+def tk_add_observer(h, rstar_obs: float, theta_obs: float) -> int:
+    k = C.c_int(-1)
+    _check(h, load_library().tk_add_observer(h, rstar_obs, theta_obs, C.byref(k)))
+    return k.value
+
+
+def tk_step(h, n: int) -> None:
+    _check(h, load_library().tk_step(h, int(n)))
+
+
+def tk_extract(h, obs_id: int, re=None, im=None):
+    """Without re/im: returns the waveform as a complex numpy array.  With two
+    CUDA tensors (or numpy arrays): fills them and returns the sample count."""
+    lib = load_library()
+    cnt = C.c_int(0)
+    if re is None:
+        _check(h, lib.tk_extract(h, obs_id, None, None, 0, C.byref(cnt), 0))
+        n = cnt.value
+        r = np.zeros(max(n, 1))
+        i = np.zeros(max(n, 1))
+        _check(h, lib.tk_extract(h, obs_id, r.ctypes.data, i.ctypes.data, n, C.byref(cnt), 0))
+        return (r + 1j * i)[:n]
+    pr, dr, kr = _arg(re)
+    pi, di, ki = _arg(im)
+    cap = min(int(np.prod(getattr(re, "shape", (0,)))), int(np.prod(getattr(im, "shape", (0,)))))
+    _check(h, lib.tk_extract(h, obs_id, pr, pi, cap, C.byref(cnt), dr))
+    if dr == 0 and isinstance(re, np.ndarray) and kr is not re:
+        re[...] = kr
+        im[...] = ki
+    return cnt.value
+
+
+def tk_get_state(h, out=None, shape=None):
+    """State as planes4 [4, Ntheta, Nr]: a new numpy array, or written into a
+    CUDA tensor ``out``."""
+    lib = load_library()
+    if out is None:
+        if shape is None:
+            raise ValueError("shape (Ntheta, Nr) is needed to allocate the host result")
+        a = np.zeros((4,) + tuple(shape))
+        _check(h, lib.tk_get_state(h, a.ctypes.data, 0))
+        return a
+    p, d, _ = _arg(out)
+    _check(h, lib.tk_get_state(h, p, d))
+    return out
+
+
+def tk_set_state(h, planes4) -> None:
+    p, d, _k = _arg(planes4)
+    _check(h, load_library().tk_set_state(h, p, d))
+
+
+def tk_steps_done(h) -> int:
+    v = C.c_int64(0)
+    _check(h, load_library().tk_steps_done(h, C.byref(v)))
+    return v.value
+
+
+def tk_check_finite(h) -> None:
+    _check(h, load_library().tk_check_finite(h))
+
+
+def tk_synchronize(h) -> None:
+    _check(h, load_library().tk_synchronize(h))
+
+
+def tk_last_error(h) -> str:
+    return load_library().tk_last_error(h).decode()
+
+
+def tk_destroy(h) -> None:
+    if h:
+        load_library().tk_destroy(h)
+
+
+# --- convenience object --------------------------------------------------------------
+class Solver:
+    """One m-mode evolution on the GPU, owning a tk_solver handle."""
+
+    def __init__(self, *, rstar_min, rstar_max, Nr, Ntheta, dt, substeps=1,
+                 variable=TK_VAR_REGULARISED, precision=TK_PREC_F64, stream=None):
+        self.Nr, self.Ntheta = int(Nr), int(Ntheta)
+        self.h = tk_make_grid(rstar_min, rstar_max, Nr, Ntheta, dt, substeps, variable,
+                              precision, stream)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            tk_destroy(h)
+            self.h = None
+
+    def close(self):
+        self.__del__()
+
+    def precompute(self, a, M, s, m):
+        tk_precompute_coeffs(self.h, a, M, s, m)
+        return self
+
+    def set_initial(self, phi_re, phi_im, pi_re=None, pi_im=None):
+        tk_set_initial_data(self.h, phi_re, phi_im, pi_re, pi_im)
+        return self
+
+    def add_observer(self, rstar, theta) -> int:
+        return tk_add_observer(self.h, rstar, theta)
+
+    def step(self, n: int):
+        tk_step(self.h, n)
+        return self
+
+    def waveform(self, obs_id: int) -> np.ndarray:
+        return tk_extract(self.h, obs_id)
+
+    def state(self, out=None):
+        return tk_get_state(self.h, out, (self.Ntheta, self.Nr))
+
+    def set_state(self, planes4):
+        tk_set_state(self.h, planes4)
+
+    def steps_done(self) -> int:
+        return tk_steps_done(self.h)
+
+    def check_finite(self):
+        tk_check_finite(self.h)
+
+    def synchronize(self):
+        tk_synchronize(self.h)

@@ -1,0 +1,316 @@
+// tk_coeffs.cu -- FP64 Kerr coefficient precompute on the device.
+//
+// 1. The tortoise coordinate (not printed in the paper) is inverted at every
+//    radial node r*_i and half node r*_{i+1/2}: x = r - r+ is found by a
+//    bracketed Newton iteration in y = ln x, so that Delta = x (r - r-) never
+//    suffers the cancellation of r^2 - 2Mr + a^2 near the horizon.
+// 2. The coefficients of the first-order system derived from Eq. 1 with the
+//    m-mode ansatz of Eq. 2 (Sec. 3.2: "matrices D and S") are evaluated at
+//    every (node, theta row) and (half node, theta row), multiplied out with
+//    dt, dr*, dtheta into the step kernel's tables, and the angular boundary
+//    conditions of Sec. 3.2 are folded into the first and last theta rows.
+#include <math.h>
+
+#include "tk_internal.h"
+
+namespace tk {
+namespace {
+
+// Horizons r+- = M +- sqrt(M^2 - a^2) and the tortoise log coefficients.
+struct Geo {
+    double M, a, rp, rm, Ap, Am;
+    int s, m;
+};
+
+__device__ Geo geometry(const Kerr &K)
+{
+    Geo g;
+    g.M = K.M;
+    g.a = K.a;
+    g.s = K.s;
+    g.m = K.m;
+    const double d = sqrt(K.M * K.M - K.a * K.a);
+    g.rp = K.M + d;
+    g.rm = K.M - d;
+    g.Ap = 2.0 * K.M * g.rp / (g.rp - g.rm);
+    g.Am = 2.0 * K.M * g.rm / (g.rp - g.rm);
+    return g;
+}
+
+__device__ double rstar_of_x(const Geo &P, double x)
+{
+    // r* = r + Ap ln((r - r+)/2M) - Am ln((r - r-)/2M),  Ap = 2M r+/(r+ - r-),
+    // Am = 2M r-/(r+ - r-); d r*/dr = (r^2 + a^2)/Delta.
+    const double r = P.rp + x;
+    return r + P.Ap * log(x / (2.0 * P.M)) - P.Am * log((r - P.rm) / (2.0 * P.M));
+}
+
+__device__ double x_of_rstar(const Geo &P, double target)
+{
+    // r*(e^y) is increasing in y with slope (r^2 + a^2)/(r - r-): keep a
+    // bracket [ylo, yhi] around the root and take Newton steps inside it,
+    // falling back to bisection when a step leaves the bracket.
+    double ylo = -700.0, yhi = 1.0;
+    for (int g = 0; g < 64 && rstar_of_x(P, exp(yhi)) < target; ++g) yhi += 1.0;
+    double y = (target > P.rp + 4.0 * P.M) ? log(target)
+                                           : (target - P.rp) / P.Ap + log(2.0 * P.M);
+    if (!(y > ylo && y < yhi)) y = 0.5 * (ylo + yhi);
+    for (int it = 0; it < 200; ++it) {
+        const double x = exp(y);
+        const double r = P.rp + x;
+        const double f = rstar_of_x(P, x) - target;
+        if (f == 0.0) break;
+        if (f < 0.0) ylo = y; else yhi = y;
+        double yn = y - f * (r - P.rm) / (r * r + P.a * P.a);
+        if (!(yn > ylo && yn < yhi)) yn = 0.5 * (ylo + yhi);
+        if (yn == y) break;
+        y = yn;
+    }
+    return exp(y);
+}
+
+__global__ void invert_tortoise_kernel(Kerr KP, double rs_min, double drs, int Nr,
+                                       double *x_node, double *x_half)
+{
+    const Geo P = geometry(KP);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < Nr) {
+        x_node[k] = x_of_rstar(P, rs_min + k * drs);
+    } else if (k < 2 * Nr - 1) {
+        const int i = k - Nr;                       // half node i + 1/2
+        x_half[i] = x_of_rstar(P, rs_min + (i + 0.5) * drs);
+    }
+}
+
+// Coefficients of   d_t Phi + b d_* Phi = Pi,
+//                   d_t Pi - b d_* Pi - c1 d_* Phi = c2 Pi + c3 Phi + c4 Phi_thth + c5 Phi_th
+// obtained from Eq. 1 x (-Delta/(Sigma^2 r^3)) with Psi = e^{i m phi} r^3 Phi and
+// Pi = d_t Phi + b d_* Phi.  With the regularised variable Phi = w Phi^ the
+// theta-singular potential is replaced by the constant -lambda0 and c5 gains
+// the 2 w'/w term.
+struct Raw {
+    double b, c1r, c1i, c2r, c2i, c3r, c3i, c4, c5;
+};
+
+__device__ Raw raw_coefficients(const Geo &P, int variable, double x, double th)
+{
+    const double M = P.M, a = P.a, s = P.s, m = P.m;
+    const double r = P.rp + x, r2 = r * r, a2 = a * a;
+    const double vp = r2 + a2;                 // varpi
+    const double Dl = x * (r - P.rm);          // Delta
+    const double dDl = 2.0 * (r - M);          // d Delta / dr
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    const double sn2 = sn * sn;
+    const double S2 = vp * vp - a2 * Dl * sn2; // Sigma^2
+    const double Sg = sqrt(S2);
+    const double b = vp / Sg;
+    const double tor = Dl / vp;                // dr/dr*
+    const double db = tor * (2.0 * r / Sg - vp * (4.0 * r * vp - a2 * dDl * sn2) / (2.0 * S2 * Sg));
+    const double fs = 3.0 * Dl / (r * vp);     // (d_* r^3)/r^3
+    const double fss = tor * ((6.0 * r * Dl + 3.0 * r2 * dDl) / vp - 6.0 * r2 * r * Dl / (vp * vp)) / (r2 * r);
+    const double Ctr = 2.0 * s * (r * Dl - M * (r2 - a2)) / S2;
+    const double Cti = (4.0 * M * a * m * r + 2.0 * s * a * Dl * cs) / S2;
+    const double E0 = (2.0 * r * Dl + s * dDl * vp) / S2;
+    const double c4 = Dl / S2;
+    double g, V;
+    if (variable == 0) {
+        g = cs / sn;
+        V = -(m + s * cs) * (m + s * cs) / sn2 + s;
+    } else {
+        const double al = 0.5 * fabs(m + s), be = 0.5 * fabs(m - s);
+        const int l0 = max(abs(P.m), abs(P.s));
+        const double t2 = tan(0.5 * th);
+        g = cs / sn + 2.0 * (al / t2 - be * t2);
+        V = -(double)(l0 - P.s) * (double)(l0 + P.s + 1);
+    }
+    Raw o;
+    o.b = b;
+    o.c1r = b * Ctr + (2.0 * b * b * fs + E0) - b * db;
+    o.c1i = b * Cti;
+    o.c2r = -Ctr;
+    o.c2i = -Cti;
+    o.c3r = b * b * fss + E0 * fs + m * m * a2 / S2 + c4 * V;
+    o.c3i = 2.0 * m * s * a * (r - M) / S2;
+    o.c4 = c4;
+    o.c5 = c4 * g;
+    return o;
+}
+
+// w(theta) = (1 - cos)^{|m+s|/2} (1 + cos)^{|m-s|/2}, written with half angles
+// (1 - cos = 2 sin^2, 1 + cos = 2 cos^2) so that nothing cancels near the poles.
+__device__ double weight_w(int s, int m, double th)
+{
+    const double sh = sin(0.5 * th), ch = cos(0.5 * th);
+    return pow(2.0 * sh * sh, 0.5 * fabs((double)(m + s))) * pow(2.0 * ch * ch, 0.5 * fabs((double)(m - s)));
+}
+
+__device__ double sl_weight(int s, int m, double th)
+{
+    const double w = weight_w(s, m, th);
+    return sin(th) * w * w;
+}
+
+// Self-adjoint stencil of the regularised angular operator on cell j:
+//   (1/P)(P F')'  ->  [P_{j+1}(F_{j+1} - F_j) - P_j (F_j - F_{j-1})] / (Q_j dth^2),
+// P = sin(theta) w^2 at the faces theta = f dth (zero on both poles), Q_j the
+// mean of P over the cell by 4-point Gauss-Legendre on 64 sub-panels.
+// ang[j] = P_{j+1}/(Q_j dth^2), ang[NP + j] = P_j/(Q_j dth^2); zero on padding rows.
+__global__ void regular_stencil_kernel(int s, int m, int Nth, int NP, double *__restrict__ ang)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= NP) return;
+    if (j >= Nth) {
+        ang[j] = 0.0;
+        ang[NP + j] = 0.0;
+        return;
+    }
+    const double dth = M_PI / Nth;
+    const double xg[2] = {0.3399810435848563, 0.8611363115940526};
+    const double wg[2] = {0.6521451548625461, 0.3478548451374538};
+    const int panels = 64;
+    const double h = dth / panels;
+    double acc = 0.0;
+    for (int k = 0; k < panels; ++k) {
+        const double c = j * dth + (k + 0.5) * h;
+        for (int g = 0; g < 2; ++g)
+            acc += wg[g] * (sl_weight(s, m, c - 0.5 * h * xg[g]) + sl_weight(s, m, c + 0.5 * h * xg[g]));
+    }
+    const double Q = 0.5 * h * acc / dth;
+    const double Plo = (j == 0) ? 0.0 : sl_weight(s, m, j * dth);
+    const double Phi = (j == Nth - 1) ? 0.0 : sl_weight(s, m, (j + 1) * dth);
+    ang[j] = Phi / (Q * dth * dth);
+    ang[NP + j] = Plo / (Q * dth * dth);
+}
+
+template <typename T>
+__global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int NP, double drs,
+                                    double dt, const double *__restrict__ x_node,
+                                    const double *__restrict__ x_half,
+                                    const double *__restrict__ ang, T *__restrict__ half,
+                                    T *__restrict__ node, double *__restrict__ b_node,
+                                    double *__restrict__ w_row)
+{
+    const int jp = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (jp >= NP || i >= Nr) return;
+    const Geo P = geometry(KP);
+    T *hcol = half + (size_t)i * kNCH * NP + jp;
+    T *ncol = node + (size_t)i * kNCN * NP + jp;
+    double hv[kNCH], nv[kNCN];
+    for (int q = 0; q < kNCH; ++q) hv[q] = 0.0;
+    for (int q = 0; q < kNCN; ++q) nv[q] = 0.0;
+    double bn = 0.0;
+    const double dth = M_PI / Nth;
+    const double ith2 = 1.0 / (dth * dth), i2th = 1.0 / (2.0 * dth);
+    const double p = (variable == 0 && (abs(P.m) & 1)) ? -1.0 : 1.0;   // ghost parity
+    if (jp < Nth) {
+        const double th = (jp + 0.5) * dth;
+        if (i == 0 && w_row) w_row[jp] = (variable != 0) ? weight_w(P.s, P.m, th) : 1.0;
+        // angular stencil A+ (row j+1), A- (row j-1); the centre gets -(A+ + A-)
+        //   literal:     A+- = 1/dth^2 +- cot(theta)/(2 dth) times c4, i.e. c4/dth^2 +- c5/(2 dth)
+        //   regularised: A+- = c4 ang[.]  (self-adjoint form, no ghosts)
+        const double Ap = (variable != 0) ? ang[jp] : 0.0;
+        const double Am = (variable != 0) ? ang[NP + jp] : 0.0;
+        {   // node r*_i, Eq. (lw2), step dt
+            const Raw c = raw_coefficients(P, variable, x_node[i], th);
+            bn = c.b;
+            if (i > 0 && i < Nr - 1) {
+                const double h2 = 0.5 * dt;
+                const double B = dt * c.b / drs;
+                const double g1r = dt * c.c1r / drs, g1i = dt * c.c1i / drs;
+                double kp, km;
+                if (variable == 0) {
+                    kp = h2 * (c.c4 * ith2 + c.c5 * i2th);
+                    km = h2 * (c.c4 * ith2 - c.c5 * i2th);
+                } else {
+                    kp = h2 * c.c4 * Ap;
+                    km = h2 * c.c4 * Am;
+                }
+                const double dg = kp + km;
+                double fpr = g1r + h2 * c.c3r - dg, fmr = -g1r + h2 * c.c3r - dg;
+                if (variable == 0 && jp == 0) { fpr += p * km; fmr += p * km; km = 0.0; }
+                if (variable == 0 && jp == Nth - 1) { fpr += p * kp; fmr += p * kp; kp = 0.0; }
+                nv[N_B] = B;
+                nv[N_PPR] = B + h2 * c.c2r;
+                nv[N_PMR] = -B + h2 * c.c2r;
+                nv[N_C2I] = h2 * c.c2i;
+                nv[N_FPR] = fpr;
+                nv[N_FPI] = g1i + h2 * c.c3i;
+                nv[N_FMR] = fmr;
+                nv[N_FMI] = -g1i + h2 * c.c3i;
+                nv[N_KP] = kp;
+                nv[N_KM] = km;
+            }
+        }
+        if (i < Nr - 1) {   // half node r*_{i+1/2}, Eq. (lw1), step dt/2
+            const Raw c = raw_coefficients(P, variable, x_half[i], th);
+            const double dtau = 0.5 * dt, e2 = 0.5 * dtau;
+            const double B = dtau * c.b / drs;
+            const double g1r = dtau * c.c1r / drs, g1i = dtau * c.c1i / drs;
+            double kp, km;
+            if (variable == 0) {
+                kp = e2 * (c.c4 * ith2 + c.c5 * i2th);
+                km = e2 * (c.c4 * ith2 - c.c5 * i2th);
+            } else {
+                kp = e2 * c.c4 * Ap;
+                km = e2 * c.c4 * Am;
+            }
+            const double dg = kp + km;
+            double far = -g1r + e2 * c.c3r - dg, fcr = g1r + e2 * c.c3r - dg;
+            if (variable == 0 && jp == 0) { far += p * km; fcr += p * km; km = 0.0; }
+            if (variable == 0 && jp == Nth - 1) { far += p * kp; fcr += p * kp; kp = 0.0; }
+            hv[H_HP] = 0.5 + B;
+            hv[H_HQ] = 0.5 - B;
+            hv[H_PAR] = 0.5 - B + e2 * c.c2r;
+            hv[H_PCR] = 0.5 + B + e2 * c.c2r;
+            hv[H_PI] = e2 * c.c2i;
+            hv[H_FAR] = far;
+            hv[H_FAI] = -g1i + e2 * c.c3i;
+            hv[H_FCR] = fcr;
+            hv[H_FCI] = g1i + e2 * c.c3i;
+            hv[H_KP] = kp;
+            hv[H_KM] = km;
+        }
+    } else if (i == 0 && w_row) {
+        w_row[jp] = 0.0;
+    }
+    for (int q = 0; q < kNCH; ++q) hcol[(size_t)q * NP] = (T)hv[q];
+    for (int q = 0; q < kNCN; ++q) ncol[(size_t)q * NP] = (T)nv[q];
+    b_node[(size_t)i * NP + jp] = bn;
+}
+
+}  // namespace
+
+cudaError_t launch_invert_tortoise(const Kerr &P, double rs_min, double drs, int Nr,
+                                   double *x_node, double *x_half, cudaStream_t st)
+{
+    const int n = 2 * Nr - 1;
+    invert_tortoise_kernel<<<(n + 127) / 128, 128, 0, st>>>(P, rs_min, drs, Nr, x_node, x_half);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coeff_tables(const Kerr &P, int variable, int Nr, int Ntheta, int NP,
+                                double drs, double dt_inner, const double *x_node,
+                                const double *x_half, double *ang, int precision, void *half,
+                                void *node, double *b_node, double *w_row, cudaStream_t st)
+{
+    if (variable != 0) {
+        regular_stencil_kernel<<<(NP + 31) / 32, 32, 0, st>>>(P.s, P.m, Ntheta, NP, ang);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    dim3 block(32, 8);
+    dim3 grid((NP + 31) / 32, (Nr + 7) / 8);
+    if (precision == 0)
+        coeff_tables_kernel<double><<<grid, block, 0, st>>>(P, variable, Nr, Ntheta, NP, drs, dt_inner,
+                                                             x_node, x_half, ang, (double *)half,
+                                                             (double *)node, b_node, w_row);
+    else
+        coeff_tables_kernel<float><<<grid, block, 0, st>>>(P, variable, Nr, Ntheta, NP, drs, dt_inner,
+                                                            x_node, x_half, ang, (float *)half,
+                                                            (float *)node, b_node, w_row);
+    return cudaGetLastError();
+}
+
+}  // namespace tk

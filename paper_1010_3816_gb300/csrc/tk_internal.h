@@ -1,0 +1,104 @@
+// tk_internal.h -- declarations shared by the CUDA translation units of libtk.
+//
+// Device-resident layout (differs from the ABI's [Ntheta][Nr] planes):
+//   state   u[i][c][jp]     i: r* column, c: 0..3 = Phi_R, Phi_I, Pi_R, Pi_I,
+//                           jp: theta row padded to NP = 32*K (rows >= Ntheta are 0)
+//   tables  half[i][q][jp]  q < kNCH: folded coefficients of Eq. (lw1) at r*_{i+1/2}
+//           node[i][q][jp]  q < kNCN: folded coefficients of Eq. (lw2) at r*_i
+// One warp owns every theta row of a column (lane l holds rows K*l .. K*l+K-1),
+// so a column of any plane or table is one contiguous, coalesced vector load.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tk {
+
+constexpr int kMaxObservers = 16;
+constexpr int kMaxK = 4;          // theta rows per lane: Ntheta <= 32 * kMaxK
+constexpr int kNCH = 11;          // half-node table entries
+constexpr int kNCN = 10;          // node table entries
+constexpr int kStepThreads = 128; // threads per block of the step kernel
+
+// Half-node table entries (Eq. lw1 with dtau = dt/2, rho = 1/dr*):
+//   HP  = 1/2 + dtau rho b        coefficient of Phi_i   in Phi^{n+1/2}
+//   HQ  = 1/2 - dtau rho b        coefficient of Phi_i+1 in Phi^{n+1/2}
+//   PAR = 1/2 - dtau rho b + dtau/2 c2R     Pi_i   -> Pi^{n+1/2} (real part)
+//   PCR = 1/2 + dtau rho b + dtau/2 c2R     Pi_i+1 -> Pi^{n+1/2} (real part)
+//   PI  = dtau/2 c2I                        imaginary part of both
+//   FA  = -dtau rho c1 + dtau/2 c3 - dtau c4/dth^2   Phi_i   -> Pi^{n+1/2} (complex)
+//   FC  = +dtau rho c1 + dtau/2 c3 - dtau c4/dth^2   Phi_i+1 -> Pi^{n+1/2} (complex)
+//   KP  = dtau/2 (c4/dth^2 + c5/(2 dth))    (Phi_i + Phi_i+1) at row j+1
+//   KM  = dtau/2 (c4/dth^2 - c5/(2 dth))    (Phi_i + Phi_i+1) at row j-1
+// plus the uniform dtau/2 on (Pi_i + Pi_i+1) in Phi^{n+1/2}.
+enum { H_HP = 0, H_HQ, H_PAR, H_PCR, H_PI, H_FAR, H_FAI, H_FCR, H_FCI, H_KP, H_KM };
+// Node table entries (Eq. lw2 with dt, applied to h+ = u^{n+1/2}_{i+1/2},
+// h- = u^{n+1/2}_{i-1/2}):
+//   B   = dt rho b              Phi^{n+1} = Phi_i - B Phi+ + B Phi- + dt/2 (Pi+ + Pi-)
+//   PPR = B + dt/2 c2R, PMR = -B + dt/2 c2R, C2I = dt/2 c2I
+//   FP  = dt rho c1 + dt/2 c3 - dt c4/dth^2,  FM = -dt rho c1 + dt/2 c3 - dt c4/dth^2
+//   KP, KM as above with dt/2.
+// Literal variable: the theta ghosts of Sec. 3.2 (u_{-1} = p u_0, u_{N} = p u_{N-1})
+// are folded into rows 0 and Ntheta-1: KM (resp. KP) is added, times p, to the
+// real parts of the two Phi coefficients and then set to 0.  Regularised
+// variable: KP, KM come from the self-adjoint stencil, which has no flux through
+// the poles (KM = 0 on row 0, KP = 0 on row Ntheta-1).  Padding rows are all 0.
+enum { N_B = 0, N_PPR, N_PMR, N_C2I, N_FPR, N_FPI, N_FMR, N_FMI, N_KP, N_KM };
+
+struct Kerr {
+    double M, a;  // black-hole mass and spin
+    int s, m;     // spin weight, azimuthal mode
+};
+
+struct ObsDev {
+    int n;                          // number of observers
+    int i0[kMaxObservers];          // lower r* column of the interpolation cell
+    int j0[kMaxObservers];          // lower theta row
+    double wr0[kMaxObservers];      // 1 - fr
+    double wr1[kMaxObservers];      // fr
+    double ft[kMaxObservers];       // theta weight fth
+};
+
+// ---- coefficient precompute (tk_coeffs.cu) ----
+cudaError_t launch_invert_tortoise(const Kerr &P, double rs_min, double drs, int Nr,
+                                   double *x_node, double *x_half, cudaStream_t st);
+cudaError_t launch_coeff_tables(const Kerr &P, int variable, int Nr, int Ntheta, int NP,
+                                double drs, double dt_inner, const double *x_node,
+                                const double *x_half, double *ang, int precision, void *half,
+                                void *node, double *b_node, double *w_row, cudaStream_t st);
+
+// ---- state import / export (tk_layout.cu) ----
+cudaError_t launch_import_state(int precision, int Nr, int Ntheta, int NP, double drs,
+                                const double *phi_re, const double *phi_im, const double *pi_re,
+                                const double *pi_im, const double *b_node, void *u,
+                                cudaStream_t st);
+cudaError_t launch_export_state(int precision, int Nr, int Ntheta, int NP, const void *u,
+                                double *planes4, cudaStream_t st);
+cudaError_t launch_finite_check(int precision, size_t n, const void *u, int *flag,
+                                cudaStream_t st);
+cudaError_t launch_wave_sum(const double *wave_obs, int64_t count, double *re, double *im,
+                            cudaStream_t st);
+
+// ---- time step (tk_step.cu) ----
+struct StepLaunch {
+    int precision, K;
+    int Nr, NP;
+    int seg;              // columns per warp
+    int warps;            // warps in the grid
+    double dt_inner;      // Lax-Wendroff step
+    const void *u_in;
+    void *u_out;
+    const void *half;
+    const void *node;
+    // waveform (only on the last inner step of an outer step)
+    int write_wave;
+    int64_t sample;       // sample index
+    int64_t wave_cap;     // samples per observer in the buffer
+    double *wave;         // [obs][cap][slot 2][re, im]
+    const double *w_row;  // w(theta_j)
+    ObsDev obs;
+};
+cudaError_t launch_lw_step(const StepLaunch &L, cudaStream_t st);
+int step_segment_length(int Nr, int K, int num_sms);
+
+}  // namespace tk

@@ -1,0 +1,102 @@
+"""Helpers for the CUDA-vs-oracle parity tests: run the same seeded workload
+through the C ABI (GPU) and through the CPU oracle, and compare.
+
+Parity is measured on the paper's fields u = {Phi_R, Phi_I, Pi_R, Pi_I}
+(Sec. 3.2).  With the pole-regularised variable the solver evolves
+Phi^ = Phi / w(theta); the physical planes are w(theta_j) times the evolved
+ones.  (Phi^ itself is badly scaled next to the poles, where w is ~1e-7: an
+O(eps) difference anywhere maps to O(eps / w) there, so Phi^ is reported
+but the bar applies to Phi.)
+
+Norms (the parity bar is 1e-12 relative L2 in FP64):
+  * per physical plane over the whole grid,
+  * per physical plane over r* >= 0 (the field near the horizon can dominate
+    the whole-grid norm on long runs),
+  * per waveform.
+A plane that is exactly zero in the oracle must be exactly zero on the GPU.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from inputs import Workload, initial_planes
+
+
+def run_oracle(w: Workload, steps=None, threads=None):
+    import oracle
+    if threads:
+        oracle.set_threads(threads)
+    sol = oracle.Solver(M=w.M, a=w.a, s=w.s, m=w.m, rs_min=w.rs_min, rs_max=w.rs_max, Nr=w.Nr,
+                        Ntheta=w.Ntheta, dt=w.dt, substeps=w.substeps, variable=w.variable)
+    ids = [sol.add_observer(r, t) for r, t in w.observers]
+    re, im = initial_planes(w)
+    sol.set_initial(re, im)
+    sol.run(w.steps if steps is None else steps)
+    return sol.state(), [sol.waveform(k) for k in ids]
+
+
+def run_gpu(w: Workload, steps=None, precision=0, device_inputs=True, chunks=1):
+    import torch
+    import paper_1010_3816_gb300 as tk
+    g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
+                  substeps=w.substeps, variable=w.variable, precision=precision)
+    try:
+        g.precompute(w.a, w.M, w.s, w.m)
+        re, im = initial_planes(w)
+        if device_inputs:
+            g.set_initial(torch.from_numpy(re).cuda(), torch.from_numpy(im).cuda())
+        else:
+            g.set_initial(re, im)
+        ids = [g.add_observer(r, t) for r, t in w.observers]
+        n = w.steps if steps is None else steps
+        done = 0
+        for c in range(chunks):
+            k = n // chunks + (1 if c < n % chunks else 0)
+            g.step(k)
+            done += k
+        assert done == n
+        return g.state(), [g.waveform(k) for k in ids]
+    finally:
+        g.close()
+
+
+def rel_l2(a, b):
+    den = np.linalg.norm(b)
+    num = np.linalg.norm(a - b)
+    if den == 0.0:
+        return 0.0 if num == 0.0 else np.inf
+    return num / den
+
+
+def row_weights(w: Workload) -> np.ndarray:
+    """w(theta_j) per theta row (1 for the literal variable), from the oracle."""
+    import math
+    import oracle
+    th = (np.arange(w.Ntheta) + 0.5) * (math.pi / w.Ntheta)
+    return np.array([oracle.weight(w.s, w.m, w.variable, t) for t in th])
+
+
+def compare(w: Workload, gpu, ref, tol=1e-12):
+    """Returns a dict of the parity numbers; asserts those of the physical
+    planes and the waveforms are <= tol (evolved-variable numbers, key
+    suffix '_evolved', are reported only)."""
+    gs, gw = gpu
+    os_, ow = ref
+    assert gs.shape == os_.shape
+    wt = row_weights(w)[None, :, None]
+    gp, op = gs * wt, os_ * wt
+    rs = w.rs_min + np.arange(w.Nr) * w.drs
+    outer = rs >= 0.0
+    out, info = {}, {}
+    for c, name in enumerate(("PhiR", "PhiI", "PiR", "PiI")):
+        out[name] = rel_l2(gp[c], op[c])
+        if outer.any():
+            out[name + "_outer"] = rel_l2(gp[c][:, outer], op[c][:, outer])
+        info[name + "_evolved"] = rel_l2(gs[c], os_[c])
+    for k, (a, b) in enumerate(zip(gw, ow)):
+        assert len(a) == len(b), (len(a), len(b))
+        out[f"wave{k}"] = rel_l2(a, b)
+    bad = {k: v for k, v in out.items() if not v <= tol}
+    assert not bad, f"parity above {tol}: {bad} (evolved variable: {info})"
+    out.update(info)
+    return out

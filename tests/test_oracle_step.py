@@ -3,8 +3,9 @@
 * kernel_average1 (Sec. 4): bit-exact half-sums.
 * Brute force: the one-step map is assembled as an explicit matrix from the
   formulas of Eqs. (lw1) and (lw2) -- averaging and difference matrices, the
-  4x4 D blocks, the source S with its centred angular stencils and ghost
-  parity, the radial edge condition -- and must reproduce the oracle's step.
+  4x4 D blocks, the source S with its centred angular stencils (ghost parity
+  for the literal field, the self-adjoint form for the regularised one), the
+  radial edge condition -- and must reproduce the oracle's step.
 * Exact symmetries of Eq. 1: a = 0 keeps real data real; a -> -a conjugates;
   m -> -m mirrors theta -> pi - theta and conjugates.
 * The initial momentum rule and the radial boundary condition.
@@ -52,7 +53,31 @@ def _angular_mats(N, parity):
     return T2, T1
 
 
-def _lw_matrix(C_node, C_half, Nr, N, drs, dt, parity):
+def _regular_mat(N, s, m):
+    """Self-adjoint centred stencil of (1/P) d_th (P d_th F), P = sin w^2, on the
+    cell-centred grid: faces at j dth carry P (zero at the poles), cells carry
+    the mean of P over the cell (here by adaptive quadrature)."""
+    from scipy.integrate import quad
+    dth = math.pi / N
+    al, be = abs(m + s) / 2, abs(m - s) / 2
+
+    def P(t):
+        return math.sin(t) * ((1 - math.cos(t)) ** al * (1 + math.cos(t)) ** be) ** 2
+
+    faces = [0.0] + [P(f * dth) for f in range(1, N)] + [0.0]
+    T = np.zeros((N, N))
+    for j in range(N):
+        Q = quad(P, j * dth, (j + 1) * dth, epsabs=0, epsrel=2e-14, limit=200)[0] / dth
+        if j > 0:
+            T[j, j - 1] += faces[j] / (Q * dth * dth)
+            T[j, j] -= faces[j] / (Q * dth * dth)
+        if j < N - 1:
+            T[j, j + 1] += faces[j + 1] / (Q * dth * dth)
+            T[j, j] -= faces[j + 1] / (Q * dth * dth)
+    return T
+
+
+def _lw_matrix(C_node, C_half, Nr, N, drs, dt, parity, regular=None):
     """Explicit matrix of one step u^n -> u^{n+1}.  State ordering: component
     k (PhiR, PhiI, PiR, PiI), then theta row j, then radial index i.
     Half nodes i + 1/2, i = 0..Nr-2, are indexed by i; the coefficient table
@@ -65,6 +90,7 @@ def _lw_matrix(C_node, C_half, Nr, N, drs, dt, parity):
 
     n_full, n_half = 4 * N * Nr, 4 * N * nh
     T2, T1 = _angular_mats(N, parity)
+    TR = None if regular is None else _regular_mat(N, *regular)
 
     def blocks(C):
         b, c1, c2, c3 = C[0], C[1] + 1j * C[2], C[3] + 1j * C[4], C[5] + 1j * C[6]
@@ -95,8 +121,9 @@ def _lw_matrix(C_node, C_half, Nr, N, drs, dt, parity):
                         Sm[Q[r], Q[s_]] += C2[r, s_]
                         Sm[Q[r], P[s_]] += C3[r, s_]
                 for jj in range(N):
+                    ang = c4 * T2[j, jj] + c5 * T1[j, jj] if TR is None else c4 * TR[j, jj]
                     for r in range(2):
-                        Sm[Q[r], vid(r, jj, c, ncol_out)] += c4 * T2[j, jj] + c5 * T1[j, jj]
+                        Sm[Q[r], vid(r, jj, c, ncol_out)] += ang
         return Dm, Sm
 
     # averaging / difference from full columns to half columns
@@ -156,7 +183,8 @@ def test_one_step_matches_explicit_matrix(oracle_mod, a, s, m, variable, Nr, N):
     u0[:, :, -1] = 0.0
     sol.set_initial(u0[0], u0[1], u0[2], u0[3])
     node, half = sol.coeffs()
-    M = _lw_matrix(node, half, Nr, N, w.drs, w.dt, oracle_mod.parity(m, variable))
+    M = _lw_matrix(node, half, Nr, N, w.drs, w.dt, oracle_mod.parity(m, variable),
+                   regular=(s, m) if variable == 1 else None)
     want = (M @ u0.reshape(-1)).reshape(4, N, Nr)
     sol.run(1)
     got = sol.state()
