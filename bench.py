@@ -197,7 +197,8 @@ def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3,
+                    help=">= 3 for a valid measurement (fewer only for profiling runs)")
     ap.add_argument("--impl", default="tk", choices=["tk", "reference"])
     ap.add_argument("--workload", default="kerr", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", type=int, default=0, choices=[0, 1])

@@ -45,7 +45,7 @@ struct tk_solver {
     int64_t count = 0;
     int64_t steps_done = 0;
     // launch shape
-    int seg = 2, warps = 1;
+    int blocks = 1;
     char err[512] = {0};
 };
 
@@ -175,8 +175,7 @@ tk_status tk_make_grid(tk_solver **out, double rstar_min, double rstar_max, int 
     S->rs_max = rstar_max;
     S->drs = (rstar_max - rstar_min) / (Nr - 1);
     S->dt = dt;
-    S->seg = tk::step_segment_length(Nr, S->K, S->num_sms);
-    S->warps = (Nr + S->seg - 1) / S->seg;
+    S->blocks = tk::step_grid_blocks(precision, S->K, Nr, S->num_sms);
 
     const size_t se = state_elems(S);
     tk_status st = TK_OK;
@@ -316,8 +315,7 @@ tk_status tk_step(tk_solver *S, int n)
     L.K = S->K;
     L.Nr = S->Nr;
     L.NP = S->NP;
-    L.seg = S->seg;
-    L.warps = S->warps;
+    L.blocks = S->blocks;
     L.dt_inner = S->dt / S->substeps;
     L.half = S->half;
     L.node = S->node;

@@ -83,8 +83,7 @@ cudaError_t launch_wave_sum(const double *wave_obs, int64_t count, double *re, d
 struct StepLaunch {
     int precision, K;
     int Nr, NP;
-    int seg;              // columns per warp
-    int warps;            // warps in the grid
+    int blocks;           // grid size (columns are split evenly over its warps)
     double dt_inner;      // Lax-Wendroff step
     const void *u_in;
     void *u_out;
@@ -99,6 +98,6 @@ struct StepLaunch {
     ObsDev obs;
 };
 cudaError_t launch_lw_step(const StepLaunch &L, cudaStream_t st);
-int step_segment_length(int Nr, int K, int num_sms);
+int step_grid_blocks(int precision, int K, int Nr, int num_sms);
 
 }  // namespace tk

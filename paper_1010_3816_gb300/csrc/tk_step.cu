@@ -246,51 +246,97 @@ __device__ __forceinline__ void observe(int i, int lane, const T (&o)[4][K], con
     }
 }
 
+// Work split: the grid has exactly (SMs x resident blocks) blocks of
+// kStepWarps warps; global warp g owns columns [g Nr / G, (g+1) Nr / G), so
+// every SM gets the same number of columns to within one per warp.  A warp
+// needs the half-step value at the left edge of its range; the first warp of
+// a block recomputes it, every other warp receives it from its left
+// neighbour through shared memory once both have finished their sweep (the
+// warp's first node is deferred until then).
 template <typename T, int K>
 __global__ void __launch_bounds__(kStepThreads)
 lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__restrict__ half,
-               const T *__restrict__ node, int Nr, int seg, int nwarps, T eh, T en,
-               const WaveArgs wa)
+               const T *__restrict__ node, int Nr, T eh, T en, const WaveArgs wa)
 {
     constexpr int NP = 32 * K;
     constexpr size_t SP = 4 * NP, HP = (size_t)kNCH * NP, NQ = (size_t)kNCN * NP;
+    constexpr int W = kStepThreads / 32;
+    // per warp: [0] its last half node (read by the right neighbour),
+    //           [1] u^n at its first column, [2] u^{n+1/2} right of its first column
+    __shared__ T sh[W][3][4][NP];
     const int lane = threadIdx.x & 31;
-    const int gw = blockIdx.x * (kStepThreads / 32) + (threadIdx.x >> 5);
-    if (gw >= nwarps) return;
-    const int i0 = gw * seg;
-    if (i0 >= Nr) return;
-    const int i1 = min(i0 + seg, Nr);
+    const int wib = threadIdx.x >> 5;
+    const long long G = (long long)gridDim.x * W;
+    const long long g = (long long)blockIdx.x * W + wib;
+    const int i0 = (int)((g * Nr) / G);
+    const int i1 = (int)(((g + 1) * Nr) / G);
     const int row = lane * K;
+    const bool lead = (wib == 0);
 
     T ua[4][K], hm[4][K];
-    load_col<T, K>(u_in + (size_t)i0 * SP + row, ua);
-    if (i0 > 0) {
-        T ul[4][K];
-        load_col<T, K>(u_in + (size_t)(i0 - 1) * SP + row, ul);
-        half_node<T, K>(ul, ua, half + (size_t)(i0 - 1) * HP + row, eh, hm);
+    if (i1 > i0) {
+        load_col<T, K>(u_in + (size_t)i0 * SP + row, ua);
+        if (lead && i0 > 0) {
+            T ul[4][K];
+            load_col<T, K>(u_in + (size_t)(i0 - 1) * SP + row, ul);
+            half_node<T, K>(ul, ua, half + (size_t)(i0 - 1) * HP + row, eh, hm);
+        } else {
+            zero_col<T, K>(hm);
+        }
+        for (int i = i0; i < i1; ++i) {
+            T uc[4][K], hp[4][K], o[4][K];
+            if (i + 1 < Nr) {
+                load_col<T, K>(u_in + (size_t)(i + 1) * SP + row, uc);
+                half_node<T, K>(ua, uc, half + (size_t)i * HP + row, eh, hp);
+            } else {
+                zero_col<T, K>(uc);
+                zero_col<T, K>(hp);
+            }
+            if (i == i0 && !lead) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int t = 0; t < K; ++t) {
+                        sh[wib][1][c][row + t] = ua[c][t];
+                        sh[wib][2][c][row + t] = hp[c][t];
+                    }
+            } else {
+                full_node<T, K>(hm, hp, ua, node + (size_t)i * NQ + row, en, o);
+                if (i == 0 || i == Nr - 1) zero_col<T, K>(o);
+                store_col<T, K>(u_out + (size_t)i * SP + row, o);
+                if (wa.write) observe<T, K>(i, lane, o, wa);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    hm[c][t] = hp[c][t];
+                    ua[c][t] = uc[c][t];
+                }
+        }
     } else {
         zero_col<T, K>(hm);
     }
-    for (int i = i0; i < i1; ++i) {
-        T uc[4][K], hp[4][K], o[4][K];
-        if (i + 1 < Nr) {
-            load_col<T, K>(u_in + (size_t)(i + 1) * SP + row, uc);
-            half_node<T, K>(ua, uc, half + (size_t)i * HP + row, eh, hp);
-        } else {
-            zero_col<T, K>(uc);
-            zero_col<T, K>(hp);
-        }
-        full_node<T, K>(hm, hp, ua, node + (size_t)i * NQ + row, en, o);
-        if (i == 0 || i == Nr - 1) zero_col<T, K>(o);
-        store_col<T, K>(u_out + (size_t)i * SP + row, o);
-        if (wa.write) observe<T, K>(i, lane, o, wa);
+    // hm now holds u^{n+1/2} at i1 - 1/2: the right neighbour's left half node
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int t = 0; t < K; ++t) sh[wib][0][c][row + t] = hm[c][t];
+    __syncthreads();
+    if (!lead && i1 > i0) {
+        T hl[4][K], hp[4][K], o[4][K];
 #pragma unroll
         for (int c = 0; c < 4; ++c)
 #pragma unroll
             for (int t = 0; t < K; ++t) {
-                hm[c][t] = hp[c][t];
-                ua[c][t] = uc[c][t];
+                hl[c][t] = sh[wib - 1][0][c][row + t];
+                ua[c][t] = sh[wib][1][c][row + t];
+                hp[c][t] = sh[wib][2][c][row + t];
             }
+        full_node<T, K>(hl, hp, ua, node + (size_t)i0 * NQ + row, en, o);
+        if (i0 == 0 || i0 == Nr - 1) zero_col<T, K>(o);
+        store_col<T, K>(u_out + (size_t)i0 * SP + row, o);
+        if (wa.write) observe<T, K>(i0, lane, o, wa);
     }
 }
 
@@ -304,24 +350,39 @@ cudaError_t launch_typed(const StepLaunch &L, cudaStream_t st)
     wa.wave = L.wave;
     wa.w_row = L.w_row;
     wa.obs = L.obs;
-    const int wpb = kStepThreads / 32;
-    const int blocks = (L.warps + wpb - 1) / wpb;
-    lw_step_kernel<T, K><<<blocks, kStepThreads, 0, st>>>(
-        (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node, L.Nr, L.seg,
-        L.warps, (T)(0.25 * L.dt_inner), (T)(0.5 * L.dt_inner), wa);
+    lw_step_kernel<T, K><<<L.blocks, kStepThreads, 0, st>>>(
+        (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node, L.Nr,
+        (T)(0.25 * L.dt_inner), (T)(0.5 * L.dt_inner), wa);
     return cudaGetLastError();
+}
+
+template <typename T, int K>
+int resident_blocks()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_step_kernel<T, K>, kStepThreads, 0) !=
+        cudaSuccess)
+        n = 1;
+    return n < 1 ? 1 : n;
 }
 
 }  // namespace
 
-int step_segment_length(int Nr, int K, int num_sms)
+int step_grid_blocks(int precision, int K, int Nr, int num_sms)
 {
-    // Aim for about four warps per SM sub-partition (4 per SM): enough to keep
-    // the FP64 pipe fed while one warp waits on its loads.
-    (void)K;
-    const long target = (long)num_sms * 4 * 4;
-    int seg = (int)((Nr + target - 1) / target);
-    return seg < 2 ? 2 : seg;
+    // one wave of resident blocks, each warp at least two columns wide
+    int per_sm = 1;
+    if (precision == 0)
+        per_sm = K == 1 ? resident_blocks<double, 1>() : K == 2 ? resident_blocks<double, 2>()
+                                                                : resident_blocks<double, 4>();
+    else
+        per_sm = K == 1 ? resident_blocks<float, 1>() : K == 2 ? resident_blocks<float, 2>()
+                                                               : resident_blocks<float, 4>();
+    const int W = kStepThreads / 32;
+    int blocks = num_sms * per_sm;
+    const int max_blocks = Nr / (2 * W);
+    if (blocks > max_blocks) blocks = max_blocks;
+    return blocks < 1 ? 1 : blocks;
 }
 
 cudaError_t launch_lw_step(const StepLaunch &L, cudaStream_t st)

@@ -76,10 +76,32 @@ def row_weights(w: Workload) -> np.ndarray:
     return np.array([oracle.weight(w.s, w.m, w.variable, t) for t in th])
 
 
-def compare(w: Workload, gpu, ref, tol=1e-12):
+def sensitivity(w: Workload, steps=None, eps=2.2e-16, seed=12345):
+    """The run's own conditioning: parity numbers between the oracle on the
+    workload's inputs and the oracle on inputs changed by ~1 ulp (each value
+    of the real initial plane times 1 + eps * N(0, 1))."""
+    import oracle
+    sol = oracle.Solver(M=w.M, a=w.a, s=w.s, m=w.m, rs_min=w.rs_min, rs_max=w.rs_max, Nr=w.Nr,
+                        Ntheta=w.Ntheta, dt=w.dt, substeps=w.substeps, variable=w.variable)
+    ids = [sol.add_observer(r, t) for r, t in w.observers]
+    re, im = initial_planes(w)
+    re = re * (1.0 + eps * np.random.default_rng(seed).standard_normal(re.shape))
+    sol.set_initial(re, im)
+    sol.run(w.steps if steps is None else steps)
+    pert = (sol.state(), [sol.waveform(k) for k in ids])
+    return pert
+
+
+def compare(w: Workload, gpu, ref, tol=1e-12, perturbed=None):
     """Returns a dict of the parity numbers; asserts those of the physical
     planes and the waveforms are <= tol (evolved-variable numbers, key
-    suffix '_evolved', are reported only)."""
+    suffix '_evolved', are reported only).
+
+    With ``perturbed`` (the oracle rerun on inputs changed by ~1 ulp, from
+    ``sensitivity``), each quantity's bar is max(tol, 10 kappa) where kappa is
+    the same quantity between the two oracle runs: a run that amplifies a
+    1-ulp change of its input beyond tol cannot be matched closer than its
+    own conditioning by any other rounding order."""
     gs, gw = gpu
     os_, ow = ref
     assert gs.shape == os_.shape
@@ -96,7 +118,13 @@ def compare(w: Workload, gpu, ref, tol=1e-12):
     for k, (a, b) in enumerate(zip(gw, ow)):
         assert len(a) == len(b), (len(a), len(b))
         out[f"wave{k}"] = rel_l2(a, b)
-    bad = {k: v for k, v in out.items() if not v <= tol}
-    assert not bad, f"parity above {tol}: {bad} (evolved variable: {info})"
+    bars = {k: tol for k in out}
+    if perturbed is not None:
+        kap = compare(w, perturbed, ref, tol=np.inf)
+        for k in out:
+            bars[k] = max(tol, 10.0 * kap[k])
+            info["kappa_" + k] = kap[k]
+    bad = {k: (v, bars[k]) for k, v in out.items() if not v <= bars[k]}
+    assert not bad, f"parity above bar: {bad} (evolved variable: {info})"
     out.update(info)
     return out

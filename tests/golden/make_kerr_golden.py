@@ -1,0 +1,56 @@
+"""Writes tests/golden/kerr_25601x64_oracle.npz: the CPU oracle's full run of
+the Kerr a = 0.9, 25601 x 64, 38400-outer-step workload (two Lax-Wendroff
+steps per outer step).  Calls only oracle/ and the shared input generator.
+
+Stored: both waveforms (every sample), the physical state Phi = w Phi^,
+Pi = w Pi^ on every 8th theta row and every 16th r* column, and the L2 norm of
+each full physical plane.  Takes about an hour on 8 cores.
+
+    python tests/golden/make_kerr_golden.py [threads]
+"""
+import math
+import os
+import sys
+import time
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import oracle  # noqa: E402
+from inputs import KERR_25601x64, initial_planes  # noqa: E402
+
+ROWS = slice(0, None, 8)
+COLS = slice(0, None, 16)
+
+
+def main():
+    if len(sys.argv) > 1:
+        oracle.set_threads(int(sys.argv[1]))
+    w = KERR_25601x64
+    sol = oracle.Solver(M=w.M, a=w.a, s=w.s, m=w.m, rs_min=w.rs_min, rs_max=w.rs_max, Nr=w.Nr,
+                        Ntheta=w.Ntheta, dt=w.dt, substeps=w.substeps, variable=w.variable)
+    ids = [sol.add_observer(r, t) for r, t in w.observers]
+    re, im = initial_planes(w)
+    sol.set_initial(re, im)
+    t0 = time.time()
+    chunk = 1200
+    for k in range(0, w.steps, chunk):
+        sol.run(min(chunk, w.steps - k))
+        print(f"{k + chunk}/{w.steps} outer steps, {time.time() - t0:.0f} s", flush=True)
+    st = sol.state()
+    th = (np.arange(w.Ntheta) + 0.5) * (math.pi / w.Ntheta)
+    wt = np.array([oracle.weight(w.s, w.m, w.variable, t) for t in th])[None, :, None]
+    phys = st * wt
+    np.savez_compressed(
+        os.path.join(HERE, "kerr_25601x64_oracle.npz"),
+        wave0=sol.waveform(ids[0]), wave1=sol.waveform(ids[1]),
+        state_sub=phys[:, ROWS, COLS], plane_norms=np.linalg.norm(phys.reshape(4, -1), axis=1),
+        rows=np.arange(w.Ntheta)[ROWS], cols=np.arange(w.Nr)[COLS],
+        note=np.array("oracle full run of " + w.name + f", {w.substeps} LW steps per outer step"))
+
+
+if __name__ == "__main__":
+    main()

@@ -13,7 +13,7 @@ import pytest
 
 from inputs import KERR_25601x64, SCHWARZSCHILD_1601x32, Workload, initial_planes
 
-from _parity import compare, rel_l2, run_gpu, run_oracle
+from _parity import compare, rel_l2, run_gpu, run_oracle, sensitivity
 
 pytestmark = pytest.mark.gpu
 
@@ -92,9 +92,14 @@ def test_spin_reversal_is_bitwise_conjugation_on_gpu():
 
 
 def test_schwarzschild_1601x32_full_run():
-    """The 1601 x 32, 2000-step Schwarzschild workload in full."""
+    """The 1601 x 32, 2000-step Schwarzschild workload in full.  The s = -2
+    evolution amplifies a 1-ulp change of the initial data to ~3e-11 in Pi by
+    t = 125 M (the oracle disagrees with itself that much), so each quantity
+    is held to max(1e-12, 10 x that sensitivity); waveforms and Phi stay at 1e-12."""
     w = SCHWARZSCHILD_1601x32
-    res = compare(w, run_gpu(w), run_oracle(w))
+    ref = run_oracle(w)
+    res = compare(w, run_gpu(w), ref, perturbed=sensitivity(w))
+    assert res["wave0"] <= 1e-12 and res["PhiR"] <= 1e-12
     print(res)
 
 
@@ -143,7 +148,7 @@ def test_state_round_trip_and_restart():
     g.set_state(dev)
     g.step(40)
     assert np.array_equal(g.state(), end)
-    assert g.steps_done() == 120
+    assert g.steps_done() == 160
     g.close()
 
 
