@@ -114,8 +114,17 @@ tk_status tk_add_observer(tk_solver *S, double rstar_obs, double theta_obs, int 
 
 /* Advance n >= 0 outer steps (Eqs. lw1 then lw2, with the theta-pole ghosts
  * and radial-edge zeros folded in), appending one sample per observer per
- * outer step.  Asynchronous. */
+ * outer step.  Asynchronous.  Whole chunks of outer steps are replayed from a
+ * CUDA graph captured on first use (see tk_set_graph_chunk); the rest are
+ * launched one by one.  Both paths run the same kernels and give identical
+ * results.  The first call after tk_add_observer, or after the waveform
+ * buffer grew, captures a new graph (host work of ~1 ms). */
 tk_status tk_step(tk_solver *S, int n);
+
+/* Outer steps per CUDA-graph replay in tk_step: -1 (default) picks about 64
+ * kernel launches per replay, 0 launches every step directly, c > 0 replays
+ * c outer steps (rounded up to an even number of launches). */
+tk_status tk_set_graph_chunk(tk_solver *S, int outer_steps);
 
 /* Waveform of observer obs_id: copies the first min(count, capacity) samples
  * into re[], im[] (device pointers if on_device) and writes the total sample
@@ -130,6 +139,21 @@ tk_status tk_get_state(tk_solver *S, double *planes4, int on_device);
  * the step counter. */
 tk_status tk_set_state(tk_solver *S, const double *planes4, int on_device);
 
+/* Largest stable inner step for the current coefficients, and the number of
+ * Lax-Wendroff steps per outer step it implies for this solver's dt.  Two
+ * limits, both evaluated on the device over every interior node: the radial
+ * CFL condition of the Lax-Wendroff scheme, b dt / dr* <= 1, and the angular
+ * source term, which the two-step scheme advances like a 2nd-order
+ * Runge-Kutta method and therefore amplifies an oscillation of frequency
+ * omega by about 1 + (omega dt)^4 / 8 per step; omega^2 is bounded by the
+ * Gershgorin radius |c3| + 2 c4 (A+ + A-) of the discrete angular operator.
+ * growth_per_step in (0, 1) is the tolerated amplification per step (e.g.
+ * 2.5e-5: a factor e over 40000 steps).  Requires tk_precompute_coeffs;
+ * synchronizes the stream.  The stiffness bound ignores a^2 couplings in the
+ * principal part and is conservative by up to ~2x in dt. */
+tk_status tk_stability_bound(tk_solver *S, double growth_per_step, double *dt_max,
+                             int *substeps_needed);
+
 /* Outer steps taken since the initial data. */
 tk_status tk_steps_done(const tk_solver *S, int64_t *steps);
 
@@ -139,6 +163,46 @@ tk_status tk_check_finite(tk_solver *S);
 
 /* Wait for all work queued by this solver. */
 tk_status tk_synchronize(tk_solver *S);
+
+/* ---- Batches: many solvers advanced together ----------------------------
+ * A batch groups n solvers (each past tk_set_initial_data, all with the same
+ * precision and outer dt, on one device) so that one kernel launch per inner
+ * Lax-Wendroff tick advances all of them.  Members may differ in every other
+ * parameter; with k_i inner steps per outer step each, an outer step is
+ * lcm(k_i) <= 64 ticks and member i steps on every (lcm/k_i)-th tick.  The
+ * batch kernel is persistent: its warps take (member, column range) items,
+ * longest first, from a queue in device memory.  Whole chunks of outer steps
+ * are replayed from a captured CUDA graph.  Results are bit-identical to
+ * stepping each member alone with tk_step.  Everything runs on the first
+ * member's stream; members must not be stepped otherwise while the batch
+ * holds them.  The batch does not own its members. */
+typedef struct tk_batch tk_batch;
+
+/* Create a batch of members[0..n-1].  TK_ERR_ARG if the members do not share
+ * device, precision and dt, or lcm(k_i) > 64. */
+tk_status tk_batch_create(tk_batch **out, tk_solver *const *members, int n);
+
+/* Advance every member by n outer steps (samples appended as by tk_step). */
+tk_status tk_batch_step(tk_batch *B, int n);
+
+/* Autotuner: time trial_steps outer steps for each candidate segment length
+ * (columns per work item: 4 .. 128) on the batch's own data, restore every
+ * member's state and sample counter after each trial, and keep the fastest.
+ * Writes the chosen length and its time per outer step (ms).  Needs device
+ * memory for one copy of every member's state. */
+tk_status tk_batch_tune(tk_batch *B, int trial_steps, int *best_seg, double *best_ms_per_step);
+
+/* Set the segment length directly (>= 2). */
+tk_status tk_batch_set_segment(tk_batch *B, int seg);
+
+/* Outer steps per graph replay: -1 automatic, 0 no graph, c > 0 about c. */
+tk_status tk_batch_set_graph_chunk(tk_batch *B, int outer_steps);
+
+/* Ticks per outer step, segment length, grid size. */
+tk_status tk_batch_info(const tk_batch *B, int *kmax, int *seg, int *blocks);
+
+const char *tk_batch_last_error(const tk_batch *B);
+void tk_batch_destroy(tk_batch *B);
 
 /* One-line description of the last error on this solver (never NULL). */
 const char *tk_last_error(const tk_solver *S);

@@ -27,8 +27,10 @@ _STATUS = {0: "TK_OK", 1: "TK_ERR_ARG", 2: "TK_ERR_STATE", 3: "TK_ERR_CUDA", 4: 
 
 # every symbol declared in include/tk.h
 EXPORTS = ("tk_make_grid", "tk_precompute_coeffs", "tk_set_initial_data", "tk_add_observer",
-           "tk_step", "tk_extract", "tk_get_state", "tk_set_state", "tk_steps_done",
-           "tk_check_finite", "tk_synchronize", "tk_last_error", "tk_destroy")
+           "tk_step", "tk_extract", "tk_get_state", "tk_set_state", "tk_stability_bound", "tk_steps_done",
+           "tk_check_finite", "tk_synchronize", "tk_last_error", "tk_destroy", "tk_set_graph_chunk",
+           "tk_batch_create", "tk_batch_step", "tk_batch_tune", "tk_batch_set_segment",
+           "tk_batch_set_graph_chunk", "tk_batch_info", "tk_batch_last_error", "tk_batch_destroy")
 
 
 class TkError(RuntimeError):
@@ -62,11 +64,21 @@ def load_library(path: str = LIB_PATH):
             "tk_extract": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, _ip, C.c_int]),
             "tk_get_state": (C.c_int, [_vp, _vp, C.c_int]),
             "tk_set_state": (C.c_int, [_vp, _vp, C.c_int]),
+            "tk_stability_bound": (C.c_int, [_vp, C.c_double, C.POINTER(C.c_double), _ip]),
             "tk_steps_done": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
             "tk_check_finite": (C.c_int, [_vp]),
+            "tk_set_graph_chunk": (C.c_int, [_vp, C.c_int]),
             "tk_synchronize": (C.c_int, [_vp]),
             "tk_last_error": (C.c_char_p, [_vp]),
             "tk_destroy": (None, [_vp]),
+            "tk_batch_create": (C.c_int, [C.POINTER(_vp), C.POINTER(_vp), C.c_int]),
+            "tk_batch_step": (C.c_int, [_vp, C.c_int]),
+            "tk_batch_tune": (C.c_int, [_vp, C.c_int, _ip, C.POINTER(C.c_double)]),
+            "tk_batch_set_segment": (C.c_int, [_vp, C.c_int]),
+            "tk_batch_set_graph_chunk": (C.c_int, [_vp, C.c_int]),
+            "tk_batch_info": (C.c_int, [_vp, _ip, _ip, _ip]),
+            "tk_batch_last_error": (C.c_char_p, [_vp]),
+            "tk_batch_destroy": (None, [_vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -187,10 +199,22 @@ def tk_set_state(h, planes4) -> None:
     _check(h, load_library().tk_set_state(h, p, d))
 
 
+def tk_stability_bound(h, growth_per_step: float = 2.5e-5):
+    """(dt_max, substeps_needed) for the current coefficients and dt."""
+    d = C.c_double(0.0)
+    k = C.c_int(0)
+    _check(h, load_library().tk_stability_bound(h, growth_per_step, C.byref(d), C.byref(k)))
+    return d.value, k.value
+
+
 def tk_steps_done(h) -> int:
     v = C.c_int64(0)
     _check(h, load_library().tk_steps_done(h, C.byref(v)))
     return v.value
+
+
+def tk_set_graph_chunk(h, outer_steps: int) -> None:
+    _check(h, load_library().tk_set_graph_chunk(h, int(outer_steps)))
 
 
 def tk_check_finite(h) -> None:
@@ -208,6 +232,54 @@ def tk_last_error(h) -> str:
 def tk_destroy(h) -> None:
     if h:
         load_library().tk_destroy(h)
+
+
+def _bcheck(b, status: int):
+    if status != TK_OK:
+        msg = load_library().tk_batch_last_error(b).decode() if b else "tk_batch_create failed"
+        raise TkError(status, msg)
+
+
+def tk_batch_create(solvers) -> C.c_void_p:
+    hs = [s.h if isinstance(s, Solver) else s for s in solvers]
+    arr = (_vp * len(hs))(*[h.value if isinstance(h, C.c_void_p) else h for h in hs])
+    b = _vp()
+    _bcheck(None, load_library().tk_batch_create(C.byref(b), arr, len(hs)))
+    return b
+
+
+def tk_batch_step(b, n: int) -> None:
+    _bcheck(b, load_library().tk_batch_step(b, int(n)))
+
+
+def tk_batch_tune(b, trial_steps: int = 3):
+    seg = C.c_int(0)
+    ms = C.c_double(0.0)
+    _bcheck(b, load_library().tk_batch_tune(b, int(trial_steps), C.byref(seg), C.byref(ms)))
+    return seg.value, ms.value
+
+
+def tk_batch_set_segment(b, seg: int) -> None:
+    _bcheck(b, load_library().tk_batch_set_segment(b, int(seg)))
+
+
+def tk_batch_set_graph_chunk(b, outer_steps: int) -> None:
+    _bcheck(b, load_library().tk_batch_set_graph_chunk(b, int(outer_steps)))
+
+
+def tk_batch_info(b):
+    k, s, bl = C.c_int(0), C.c_int(0), C.c_int(0)
+    _bcheck(b, load_library().tk_batch_info(b, C.byref(k), C.byref(s), C.byref(bl)))
+    return {"kmax": k.value, "seg": s.value, "blocks": bl.value}
+
+
+def tk_batch_last_error(b) -> str:
+    return load_library().tk_batch_last_error(b).decode()
+
+
+def tk_batch_destroy(b) -> None:
+    if b:
+        load_library().tk_batch_destroy(b)
 
 
 # --- convenience object --------------------------------------------------------------
@@ -253,6 +325,13 @@ class Solver:
     def set_state(self, planes4):
         tk_set_state(self.h, planes4)
 
+    def set_graph_chunk(self, outer_steps: int):
+        tk_set_graph_chunk(self.h, outer_steps)
+        return self
+
+    def stability_bound(self, growth_per_step: float = 2.5e-5):
+        return tk_stability_bound(self.h, growth_per_step)
+
     def steps_done(self) -> int:
         return tk_steps_done(self.h)
 
@@ -261,3 +340,39 @@ class Solver:
 
     def synchronize(self):
         tk_synchronize(self.h)
+
+
+class Batch:
+    """Several Solver objects advanced together (tk_batch_*).  Keeps its
+    members alive."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.b = tk_batch_create(self.solvers)
+
+    def __del__(self):
+        b = getattr(self, "b", None)
+        if b:
+            tk_batch_destroy(b)
+            self.b = None
+
+    def close(self):
+        self.__del__()
+
+    def step(self, n: int):
+        tk_batch_step(self.b, n)
+        return self
+
+    def tune(self, trial_steps: int = 3):
+        return tk_batch_tune(self.b, trial_steps)
+
+    def set_segment(self, seg: int):
+        tk_batch_set_segment(self.b, seg)
+        return self
+
+    def set_graph_chunk(self, outer_steps: int):
+        tk_batch_set_graph_chunk(self.b, outer_steps)
+        return self
+
+    def info(self):
+        return tk_batch_info(self.b)

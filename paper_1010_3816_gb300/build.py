@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtk.so")
-SOURCES = ["tk_api.cu", "tk_coeffs.cu", "tk_step.cu", "tk_layout.cu"]
+SOURCES = ["tk_api.cu", "tk_coeffs.cu", "tk_step.cu", "tk_layout.cu", "tk_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -38,7 +38,7 @@ def _stale(target: str, deps) -> bool:
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     """Compile and link libtk.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+    headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
     headers.append(os.path.join(ROOT, "include", "tk.h"))
     cc = nvcc()
 

@@ -11,47 +11,13 @@
 
 #include <new>
 
-#include "tk.h"
-#include "tk_internal.h"
-
-struct tk_solver {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int num_sms = 0;
-    // grid
-    int Nr = 0, Nth = 0, K = 1, NP = 32, substeps = 1, variable = 1, precision = 0;
-    double rs_min = 0, rs_max = 0, drs = 0, dt = 0;
-    size_t esz = 8;
-    // device buffers
-    void *u[2] = {nullptr, nullptr};
-    int cur = 0;
-    void *half = nullptr, *node = nullptr;
-    double *b_node = nullptr, *w_row = nullptr, *x_node = nullptr, *x_half = nullptr;
-    double *ang = nullptr;      // regularised angular stencil [2][NP]
-    double *staging = nullptr;  // 4 * Nth * Nr doubles, for host transfers
-    int *flag = nullptr;
-    // physics
-    tk::Kerr kerr{};
-    bool have_coeffs = false, have_state = false;
-    // observers and waveform samples
-    struct Obs {
-        double rs, th;
-        int i0, j0;
-        double fr, ft;
-    } obs[tk::kMaxObservers];
-    int nobs = 0;
-    double *wave = nullptr;  // [obs][cap][2 slots][re, im]
-    int64_t wave_cap = 0;
-    int64_t count = 0;
-    int64_t steps_done = 0;
-    // launch shape
-    int blocks = 1;
-    char err[512] = {0};
-};
+#include "tk_solver_impl.h"
 
 namespace {
-
 thread_local char g_err[512] = "no error";
+}  // namespace
+
+namespace tkh {
 
 tk_status fail(tk_solver *S, tk_status st, const char *fmt, ...)
 {
@@ -62,14 +28,6 @@ tk_status fail(tk_solver *S, tk_status st, const char *fmt, ...)
     va_end(ap);
     return st;
 }
-
-#define TK_CUDA(S, call)                                                                  \
-    do {                                                                                  \
-        cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess)                                                            \
-            return fail((S), e_ == cudaErrorMemoryAllocation ? TK_ERR_OOM : TK_ERR_CUDA,  \
-                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-    } while (0)
 
 size_t state_elems(const tk_solver *S) { return (size_t)S->Nr * 4 * S->NP; }
 
@@ -87,9 +45,12 @@ tk_status alloc(tk_solver *S, void **p, size_t bytes)
 void release(tk_solver *S)
 {
     void *ptrs[] = {S->u[0], S->u[1], S->half, S->node, S->b_node, S->w_row,
-                    S->x_node, S->x_half, S->ang, S->staging, S->flag, S->wave};
+                    S->x_node, S->x_half, S->ang, S->staging, S->flag, S->stiff, S->ctr, S->wave};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (int k = 0; k < 2; ++k)
+        if (S->graph[k]) cudaGraphExecDestroy(S->graph[k]);
+    if (S->capture_stream) cudaStreamDestroy(S->capture_stream);
 }
 
 tk_status ensure_staging(tk_solver *S)
@@ -120,6 +81,7 @@ tk_status ensure_wave(tk_solver *S, int64_t need)
     if (S->wave) cudaFree(S->wave);
     S->wave = nw;
     S->wave_cap = cap;
+    S->epoch++;
     return TK_OK;
 }
 
@@ -130,7 +92,40 @@ tk_status enter(tk_solver *S)
     return TK_OK;
 }
 
-}  // namespace
+void fill_launch(const tk_solver *S, tk::StepLaunch &L)
+{
+    L.precision = S->precision;
+    L.K = S->K;
+    L.Nr = S->Nr;
+    L.NP = S->NP;
+    L.blocks = S->blocks;
+    L.dt_inner = S->dt / S->substeps;
+    L.half = S->half;
+    L.node = S->node;
+    L.wave_cap = S->wave_cap;
+    L.wave = S->wave;
+    L.w_row = S->w_row;
+    L.sample_ctr = S->ctr;
+    L.done_ctr = (unsigned int *)(S->ctr + 1);
+    L.obs.n = S->nobs;
+    for (int k = 0; k < S->nobs; ++k) {
+        L.obs.i0[k] = S->obs[k].i0;
+        L.obs.j0[k] = S->obs[k].j0;
+        L.obs.wr0[k] = 1.0 - S->obs[k].fr;
+        L.obs.wr1[k] = S->obs[k].fr;
+        L.obs.ft[k] = S->obs[k].ft;
+    }
+}
+
+}  // namespace tkh
+
+using tkh::alloc;
+using tkh::ensure_staging;
+using tkh::release;
+using tkh::state_elems;
+using tkh::enter;
+using tkh::ensure_wave;
+using tkh::fail;
 
 extern "C" {
 
@@ -189,6 +184,8 @@ tk_status tk_make_grid(tk_solver **out, double rstar_min, double rstar_max, int 
     if (st == TK_OK) st = alloc(S, (void **)&S->x_half, (size_t)Nr * sizeof(double));
     if (st == TK_OK) st = alloc(S, (void **)&S->ang, (size_t)2 * S->NP * sizeof(double));
     if (st == TK_OK) st = alloc(S, (void **)&S->flag, sizeof(int));
+    if (st == TK_OK) st = alloc(S, (void **)&S->stiff, 2 * sizeof(unsigned long long));
+    if (st == TK_OK) st = alloc(S, (void **)&S->ctr, 2 * sizeof(long long));
     if (st != TK_OK) {
         snprintf(g_err, sizeof g_err, "%s", S->err);
         release(S);
@@ -197,6 +194,7 @@ tk_status tk_make_grid(tk_solver **out, double rstar_min, double rstar_max, int 
     }
     e = cudaMemsetAsync(S->u[0], 0, se * S->esz, S->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(S->u[1], 0, se * S->esz, S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->ctr, 0, 2 * sizeof(long long), S->stream);
     if (e != cudaSuccess) {
         fail(nullptr, TK_ERR_CUDA, "tk_make_grid: %s", cudaGetErrorString(e));
         release(S);
@@ -266,6 +264,7 @@ tk_status tk_set_initial_data(tk_solver *S, const double *phi_re, const double *
         return fail(S, TK_ERR_ARG, "tk_set_initial_data: give both pi planes or neither");
     st = import_planes(S, phi_re, phi_im, pi_re, pi_im, on_device);
     if (st != TK_OK) return st;
+    TK_CUDA(S, cudaMemsetAsync(S->ctr, 0, 2 * sizeof(long long), S->stream));
     S->have_state = true;
     S->count = 0;
     S->steps_done = 0;
@@ -298,6 +297,72 @@ tk_status tk_add_observer(tk_solver *S, double rstar_obs, double theta_obs, int 
     o.fr = fi - i0;
     o.ft = fj - j0;
     *obs_id = S->nobs++;
+    S->epoch++;
+    return TK_OK;
+}
+
+// Enqueue `outer` outer steps starting from level `cur` on stream `st`;
+// returns the level holding the result.
+static cudaError_t enqueue_steps(const tk_solver *S, int cur, int outer, cudaStream_t st, int *cur_out)
+{
+    tk::StepLaunch L;
+    tkh::fill_launch(S, L);
+    for (int it = 0; it < outer; ++it)
+        for (int k = 0; k < S->substeps; ++k) {
+            L.u_in = S->u[cur];
+            L.u_out = S->u[cur ^ 1];
+            L.write_wave = (k == S->substeps - 1) && S->nobs > 0;
+            cudaError_t e = tk::launch_lw_step(L, st);
+            if (e != cudaSuccess) return e;
+            cur ^= 1;
+        }
+    *cur_out = cur;
+    return cudaSuccess;
+}
+
+static int graph_chunk(const tk_solver *S)
+{
+    if (S->graph_chunk >= 0) {
+        // an even number of launches per replay keeps the ping-pong level fixed
+        int c = S->graph_chunk;
+        if (c > 0 && ((long long)c * S->substeps) % 2) ++c;
+        return c;
+    }
+    // automatic: about 64 launches per replay, rounded to an even launch count
+    int c = (64 + S->substeps - 1) / S->substeps;
+    if (((long long)c * S->substeps) % 2) ++c;
+    return c;
+}
+
+static tk_status get_graph(tk_solver *S, int chunk, cudaGraphExec_t *out)
+{
+    const int p = S->cur;
+    if (S->graph[p] && S->graph_epoch[p] == S->epoch && S->graph_outer[p] == chunk) {
+        *out = S->graph[p];
+        return TK_OK;
+    }
+    if (S->graph[p]) {
+        cudaGraphExecDestroy(S->graph[p]);
+        S->graph[p] = nullptr;
+    }
+    if (!S->capture_stream)
+        TK_CUDA(S, cudaStreamCreateWithFlags(&S->capture_stream, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    TK_CUDA(S, cudaStreamBeginCapture(S->capture_stream, cudaStreamCaptureModeThreadLocal));
+    int cur_after = p;
+    cudaError_t e = enqueue_steps(S, p, chunk, S->capture_stream, &cur_after);
+    cudaError_t e2 = cudaStreamEndCapture(S->capture_stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess && cur_after != p) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&S->graph[p], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        S->graph[p] = nullptr;
+        return fail(S, TK_ERR_CUDA, "tk_step: graph capture failed: %s", cudaGetErrorString(e));
+    }
+    S->graph_epoch[p] = S->epoch;
+    S->graph_outer[p] = chunk;
+    *out = S->graph[p];
     return TK_OK;
 }
 
@@ -310,38 +375,33 @@ tk_status tk_step(tk_solver *S, int n)
     if (n == 0) return TK_OK;
     st = ensure_wave(S, S->count + n);
     if (st != TK_OK) return st;
-    tk::StepLaunch L;
-    L.precision = S->precision;
-    L.K = S->K;
-    L.Nr = S->Nr;
-    L.NP = S->NP;
-    L.blocks = S->blocks;
-    L.dt_inner = S->dt / S->substeps;
-    L.half = S->half;
-    L.node = S->node;
-    L.wave_cap = S->wave_cap;
-    L.wave = S->wave;
-    L.w_row = S->w_row;
-    L.obs.n = S->nobs;
-    for (int k = 0; k < S->nobs; ++k) {
-        L.obs.i0[k] = S->obs[k].i0;
-        L.obs.j0[k] = S->obs[k].j0;
-        L.obs.wr0[k] = 1.0 - S->obs[k].fr;
-        L.obs.wr1[k] = S->obs[k].fr;
-        L.obs.ft[k] = S->obs[k].ft;
+    const int chunk = graph_chunk(S);
+    while (chunk > 0 && n >= chunk) {
+        cudaGraphExec_t ge = nullptr;
+        st = get_graph(S, chunk, &ge);
+        if (st != TK_OK) return st;
+        TK_CUDA(S, cudaGraphLaunch(ge, S->stream));
+        S->count += chunk;
+        S->steps_done += chunk;
+        n -= chunk;
     }
-    for (int it = 0; it < n; ++it) {
-        for (int k = 0; k < S->substeps; ++k) {
-            L.u_in = S->u[S->cur];
-            L.u_out = S->u[S->cur ^ 1];
-            L.write_wave = (k == S->substeps - 1) && S->nobs > 0;
-            L.sample = S->count;
-            TK_CUDA(S, tk::launch_lw_step(L, S->stream));
-            S->cur ^= 1;
-        }
-        S->count++;
-        S->steps_done++;
+    if (n > 0) {
+        int cur = S->cur;
+        TK_CUDA(S, enqueue_steps(S, S->cur, n, S->stream, &cur));
+        S->cur = cur;
+        S->count += n;
+        S->steps_done += n;
     }
+    return TK_OK;
+}
+
+tk_status tk_set_graph_chunk(tk_solver *S, int outer_steps)
+{
+    tk_status st = enter(S);
+    if (st != TK_OK) return st;
+    if (outer_steps < -1) return fail(S, TK_ERR_ARG, "tk_set_graph_chunk: %d < -1", outer_steps);
+    S->graph_chunk = outer_steps;
+    S->epoch++;
     return TK_OK;
 }
 
@@ -402,6 +462,34 @@ tk_status tk_set_state(tk_solver *S, const double *planes4, int on_device)
     if (!planes4) return fail(S, TK_ERR_ARG, "tk_set_state: planes4 is NULL");
     const size_t plane = (size_t)S->Nth * S->Nr;
     return import_planes(S, planes4, planes4 + plane, planes4 + 2 * plane, planes4 + 3 * plane, on_device);
+}
+
+tk_status tk_stability_bound(tk_solver *S, double growth_per_step, double *dt_max,
+                             int *substeps_needed)
+{
+    tk_status st = enter(S);
+    if (st != TK_OK) return st;
+    if (!S->have_coeffs) return fail(S, TK_ERR_STATE, "tk_stability_bound before tk_precompute_coeffs");
+    if (!dt_max || !substeps_needed) return fail(S, TK_ERR_ARG, "tk_stability_bound: NULL output");
+    if (!(growth_per_step > 0.0) || !(growth_per_step < 1.0))
+        return fail(S, TK_ERR_ARG, "tk_stability_bound: growth_per_step must be in (0, 1)");
+    unsigned long long h[2] = {0, 0};
+    TK_CUDA(S, tk::launch_stiffness(S->kerr, S->variable, S->Nr, S->Nth, S->NP, S->x_node, S->ang,
+                                    S->stiff, S->stream));
+    TK_CUDA(S, cudaMemcpyAsync(h, S->stiff, sizeof h, cudaMemcpyDeviceToHost, S->stream));
+    TK_CUDA(S, cudaStreamSynchronize(S->stream));
+    double w2, bmax;
+    memcpy(&w2, &h[0], sizeof w2);
+    memcpy(&bmax, &h[1], sizeof bmax);
+    // radial CFL of the Lax-Wendroff scheme: b dt / dr* <= 1
+    double dt = bmax > 0.0 ? S->drs / bmax : INFINITY;
+    // angular source term: per step the fastest mode grows by ~ (omega dt)^4 / 8
+    const double zmax = pow(8.0 * growth_per_step, 0.25);
+    if (w2 > 0.0) dt = fmin(dt, zmax / sqrt(w2));
+    *dt_max = dt;
+    const double k = ceil(S->dt / dt * (1.0 - 1e-12));
+    *substeps_needed = k < 1.0 ? 1 : (k > 1e9 ? 1000000000 : (int)k);
+    return TK_OK;
 }
 
 tk_status tk_steps_done(const tk_solver *S, int64_t *steps)

@@ -280,7 +280,50 @@ __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int 
     b_node[(size_t)i * NP + jp] = bn;
 }
 
+// Stiffness of the source term at every interior node: a Gershgorin bound on
+// the spectrum of the Phi -> Pi coupling c3 + c4 (angular stencil), i.e. on
+// omega^2 of the fastest angular oscillation, and the radial speed b.  The two
+// maxima are written as the bit patterns of non-negative doubles, which order
+// like unsigned integers: out[0] = max omega^2, out[1] = max b.
+__global__ void stiffness_kernel(Kerr KP, int variable, int Nr, int Nth, int NP,
+                                 const double *__restrict__ x_node, const double *__restrict__ ang,
+                                 unsigned long long *__restrict__ out)
+{
+    const int jp = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    double w2 = 0.0, bb = 0.0;
+    if (jp < Nth && i > 0 && i < Nr - 1) {
+        const Geo P = geometry(KP);
+        const double dth = M_PI / Nth;
+        const double th = (jp + 0.5) * dth;
+        const Raw c = raw_coefficients(P, variable, x_node[i], th);
+        const double asum = (variable != 0) ? ang[jp] + ang[NP + jp] : 2.0 / (dth * dth);
+        w2 = sqrt(c.c3r * c.c3r + c.c3i * c.c3i) + 2.0 * c.c4 * asum;
+        bb = c.b;
+    }
+    // warp maximum, then one atomic per warp
+    for (int off = 16; off > 0; off >>= 1) {
+        w2 = fmax(w2, __shfl_xor_sync(0xffffffffu, w2, off));
+        bb = fmax(bb, __shfl_xor_sync(0xffffffffu, bb, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(w2));
+        atomicMax(out + 1, (unsigned long long)__double_as_longlong(bb));
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_stiffness(const Kerr &P, int variable, int Nr, int Ntheta, int NP,
+                             const double *x_node, const double *ang, unsigned long long *out,
+                             cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    dim3 block(32, 8), grid((NP + 31) / 32, (Nr + 7) / 8);
+    stiffness_kernel<<<grid, block, 0, st>>>(P, variable, Nr, Ntheta, NP, x_node, ang, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_invert_tortoise(const Kerr &P, double rs_min, double drs, int Nr,
                                    double *x_node, double *x_half, cudaStream_t st)

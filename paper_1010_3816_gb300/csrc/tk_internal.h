@@ -67,6 +67,10 @@ cudaError_t launch_coeff_tables(const Kerr &P, int variable, int Nr, int Ntheta,
                                 const double *x_half, double *ang, int precision, void *half,
                                 void *node, double *b_node, double *w_row, cudaStream_t st);
 
+cudaError_t launch_stiffness(const Kerr &P, int variable, int Nr, int Ntheta, int NP,
+                             const double *x_node, const double *ang, unsigned long long *out,
+                             cudaStream_t st);
+
 // ---- state import / export (tk_layout.cu) ----
 cudaError_t launch_import_state(int precision, int Nr, int Ntheta, int NP, double drs,
                                 const double *phi_re, const double *phi_im, const double *pi_re,
@@ -91,7 +95,8 @@ struct StepLaunch {
     const void *node;
     // waveform (only on the last inner step of an outer step)
     int write_wave;
-    int64_t sample;       // sample index
+    const long long *sample_ctr;  // device: index of the sample the outer step writes
+    unsigned int *done_ctr;       // device: blocks finished (reset by the last one)
     int64_t wave_cap;     // samples per observer in the buffer
     double *wave;         // [obs][cap][slot 2][re, im]
     const double *w_row;  // w(theta_j)

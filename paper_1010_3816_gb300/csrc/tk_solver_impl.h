@@ -1,0 +1,71 @@
+// tk_solver_impl.h -- the solver object behind the opaque tk_solver handle,
+// and the host helpers shared by tk_api.cu and tk_batch.cu.
+#pragma once
+
+#include <stdint.h>
+
+#include "tk.h"
+#include "tk_internal.h"
+
+struct tk_solver {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    // grid
+    int Nr = 0, Nth = 0, K = 1, NP = 32, substeps = 1, variable = 1, precision = 0;
+    double rs_min = 0, rs_max = 0, drs = 0, dt = 0;
+    size_t esz = 8;
+    // device buffers
+    void *u[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *half = nullptr, *node = nullptr;
+    double *b_node = nullptr, *w_row = nullptr, *x_node = nullptr, *x_half = nullptr;
+    double *ang = nullptr;      // regularised angular stencil [2][NP]
+    double *staging = nullptr;  // 4 * Nth * Nr doubles, for host transfers
+    int *flag = nullptr;
+    unsigned long long *stiff = nullptr;  // [max omega^2, max b] as double bit patterns
+    long long *ctr = nullptr;   // [0]: sample index of the next outer step, [1]: blocks done
+    // physics
+    tk::Kerr kerr{};
+    bool have_coeffs = false, have_state = false;
+    // observers and waveform samples
+    struct Obs {
+        double rs, th;
+        int i0, j0;
+        double fr, ft;
+    } obs[tk::kMaxObservers];
+    int nobs = 0;
+    double *wave = nullptr;  // [obs][cap][2 slots][re, im]
+    int64_t wave_cap = 0;
+    int64_t count = 0;
+    int64_t steps_done = 0;
+    // launch shape
+    int blocks = 1;
+    // CUDA-graph replay of chunks of outer steps (0 = launch every step directly)
+    int graph_chunk = -1;            // -1: choose automatically
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};   // by parity of the current level
+    int graph_outer[2] = {0, 0};
+    long long graph_epoch[2] = {-1, -1};
+    long long epoch = 0;             // bumped whenever captured parameters change
+    char err[512] = {0};
+};
+
+namespace tkh {
+
+// Record a one-line message on the solver (or thread-locally if S is NULL).
+tk_status fail(tk_solver *S, tk_status st, const char *fmt, ...);
+tk_status alloc(tk_solver *S, void **p, size_t bytes);
+tk_status ensure_wave(tk_solver *S, int64_t need);
+tk_status enter(tk_solver *S);
+void fill_launch(const tk_solver *S, tk::StepLaunch &L);
+
+}  // namespace tkh
+
+#define TK_CUDA(S, call)                                                                  \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return tkh::fail((S), e_ == cudaErrorMemoryAllocation ? TK_ERR_OOM : TK_ERR_CUDA, \
+                             "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)

@@ -16,232 +16,36 @@
 // theta-pole boundary conditions are folded into the coefficient tables, so
 // the arithmetic is branch-free: 28 FP64 (or FP32) operations per half node
 // and 28 per node.  A segment recomputes one half node at its left end.
-#include "tk_internal.h"
+#include "tk_stencil.cuh"
 
 namespace tk {
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-template <typename T, int K>
-__device__ __forceinline__ void ldk(const T *__restrict__ p, T (&v)[K])
-{
-    if constexpr (sizeof(T) == 8 && K == 1) {
-        v[0] = p[0];
-    } else if constexpr (sizeof(T) == 8) {
-#pragma unroll
-        for (int t = 0; t < K; t += 2) {
-            const double2 x = *reinterpret_cast<const double2 *>(p + t);
-            v[t] = x.x;
-            v[t + 1] = x.y;
-        }
-    } else if constexpr (K == 1) {
-        v[0] = p[0];
-    } else if constexpr (K == 2) {
-        const float2 x = *reinterpret_cast<const float2 *>(p);
-        v[0] = x.x;
-        v[1] = x.y;
-    } else {
-        const float4 x = *reinterpret_cast<const float4 *>(p);
-        v[0] = x.x;
-        v[1] = x.y;
-        v[2] = x.z;
-        v[3] = x.w;
-    }
-}
-
-template <typename T, int K>
-__device__ __forceinline__ void stk(T *__restrict__ p, const T (&v)[K])
-{
-    if constexpr (sizeof(T) == 8 && K == 1) {
-        p[0] = v[0];
-    } else if constexpr (sizeof(T) == 8) {
-#pragma unroll
-        for (int t = 0; t < K; t += 2) *reinterpret_cast<double2 *>(p + t) = make_double2(v[t], v[t + 1]);
-    } else if constexpr (K == 1) {
-        p[0] = v[0];
-    } else if constexpr (K == 2) {
-        *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
-    } else {
-        *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    }
-}
-
-template <typename T, int K>
-__device__ __forceinline__ void load_col(const T *__restrict__ p, T (&u)[4][K])
-{
-    constexpr int NP = 32 * K;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) ldk<T, K>(p + c * NP, u[c]);
-}
-
-template <typename T, int K>
-__device__ __forceinline__ void store_col(T *__restrict__ p, const T (&u)[4][K])
-{
-    constexpr int NP = 32 * K;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) stk<T, K>(p + c * NP, u[c]);
-}
-
-template <typename T, int K>
-__device__ __forceinline__ void zero_col(T (&u)[4][K])
-{
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int t = 0; t < K; ++t) u[c][t] = T(0);
-}
-
-// Neighbouring-row values of s (row j+1 -> up, row j-1 -> dn) for every row
-// a lane holds.  Lane 0's j-1 and lane 31's j+1 read their own values; the
-// folded tables give those terms a zero coefficient.
-template <typename T, int K>
-__device__ __forceinline__ void theta_neighbours(const T (&s)[K], T (&up)[K], T (&dn)[K])
-{
-    const T nxt = __shfl_down_sync(kFull, s[0], 1);
-    const T prv = __shfl_up_sync(kFull, s[K - 1], 1);
-#pragma unroll
-    for (int t = 0; t < K; ++t) {
-        up[t] = (t + 1 < K) ? s[t + 1] : nxt;
-        dn[t] = (t > 0) ? s[t - 1] : prv;
-    }
-}
-
-// Eq. (lw1): u^{n+1/2}_{i+1/2} from a = u^n_i and c = u^n_{i+1}.
-template <typename T, int K>
-__device__ __forceinline__ void half_node(const T (&a)[4][K], const T (&c)[4][K],
-                                          const T *__restrict__ tab, const T e, T (&h)[4][K])
-{
-    constexpr int NP = 32 * K;
-    T sR[K], sI[K], upR[K], upI[K], dnR[K], dnI[K];
-#pragma unroll
-    for (int t = 0; t < K; ++t) {
-        sR[t] = a[0][t] + c[0][t];
-        sI[t] = a[1][t] + c[1][t];
-    }
-    theta_neighbours<T, K>(sR, upR, dnR);
-    theta_neighbours<T, K>(sI, upI, dnI);
-    T q[kNCH][K];
-#pragma unroll
-    for (int k = 0; k < kNCH; ++k) ldk<T, K>(tab + k * NP, q[k]);
-#pragma unroll
-    for (int t = 0; t < K; ++t) {
-        const T sPR = a[2][t] + c[2][t];
-        const T sPI = a[3][t] + c[3][t];
-        h[0][t] = fma(q[H_HQ][t], c[0][t], fma(q[H_HP][t], a[0][t], e * sPR));
-        h[1][t] = fma(q[H_HQ][t], c[1][t], fma(q[H_HP][t], a[1][t], e * sPI));
-        T x = q[H_PAR][t] * a[2][t];
-        x = fma(q[H_PCR][t], c[2][t], x);
-        x = fma(-q[H_PI][t], sPI, x);
-        x = fma(q[H_FAR][t], a[0][t], x);
-        x = fma(-q[H_FAI][t], a[1][t], x);
-        x = fma(q[H_FCR][t], c[0][t], x);
-        x = fma(-q[H_FCI][t], c[1][t], x);
-        x = fma(q[H_KP][t], upR[t], x);
-        x = fma(q[H_KM][t], dnR[t], x);
-        h[2][t] = x;
-        T y = q[H_PAR][t] * a[3][t];
-        y = fma(q[H_PCR][t], c[3][t], y);
-        y = fma(q[H_PI][t], sPR, y);
-        y = fma(q[H_FAR][t], a[1][t], y);
-        y = fma(q[H_FAI][t], a[0][t], y);
-        y = fma(q[H_FCR][t], c[1][t], y);
-        y = fma(q[H_FCI][t], c[0][t], y);
-        y = fma(q[H_KP][t], upI[t], y);
-        y = fma(q[H_KM][t], dnI[t], y);
-        h[3][t] = y;
-    }
-}
-
-// Eq. (lw2): u^{n+1}_i from hm = u^{n+1/2}_{i-1/2}, hp = u^{n+1/2}_{i+1/2}, u = u^n_i.
-template <typename T, int K>
-__device__ __forceinline__ void full_node(const T (&hm)[4][K], const T (&hp)[4][K],
-                                          const T (&u)[4][K], const T *__restrict__ tab,
-                                          const T e, T (&o)[4][K])
-{
-    constexpr int NP = 32 * K;
-    T sR[K], sI[K], upR[K], upI[K], dnR[K], dnI[K];
-#pragma unroll
-    for (int t = 0; t < K; ++t) {
-        sR[t] = hp[0][t] + hm[0][t];
-        sI[t] = hp[1][t] + hm[1][t];
-    }
-    theta_neighbours<T, K>(sR, upR, dnR);
-    theta_neighbours<T, K>(sI, upI, dnI);
-    T q[kNCN][K];
-#pragma unroll
-    for (int k = 0; k < kNCN; ++k) ldk<T, K>(tab + k * NP, q[k]);
-#pragma unroll
-    for (int t = 0; t < K; ++t) {
-        const T sPR = hp[2][t] + hm[2][t];
-        const T sPI = hp[3][t] + hm[3][t];
-        o[0][t] = fma(e, sPR, fma(q[N_B][t], hm[0][t], fma(-q[N_B][t], hp[0][t], u[0][t])));
-        o[1][t] = fma(e, sPI, fma(q[N_B][t], hm[1][t], fma(-q[N_B][t], hp[1][t], u[1][t])));
-        T x = fma(q[N_PPR][t], hp[2][t], u[2][t]);
-        x = fma(q[N_PMR][t], hm[2][t], x);
-        x = fma(-q[N_C2I][t], sPI, x);
-        x = fma(q[N_FPR][t], hp[0][t], x);
-        x = fma(-q[N_FPI][t], hp[1][t], x);
-        x = fma(q[N_FMR][t], hm[0][t], x);
-        x = fma(-q[N_FMI][t], hm[1][t], x);
-        x = fma(q[N_KP][t], upR[t], x);
-        x = fma(q[N_KM][t], dnR[t], x);
-        o[2][t] = x;
-        T y = fma(q[N_PPR][t], hp[3][t], u[3][t]);
-        y = fma(q[N_PMR][t], hm[3][t], y);
-        y = fma(q[N_C2I][t], sPR, y);
-        y = fma(q[N_FPR][t], hp[1][t], y);
-        y = fma(q[N_FPI][t], hp[0][t], y);
-        y = fma(q[N_FMR][t], hm[1][t], y);
-        y = fma(q[N_FMI][t], hm[0][t], y);
-        y = fma(q[N_KP][t], upI[t], y);
-        y = fma(q[N_KM][t], dnI[t], y);
-        o[3][t] = y;
-    }
-}
-
 struct WaveArgs {
     int write;
-    int64_t sample, cap;
+    int64_t cap;
+    const long long *sample;   // device counter: index of the sample this outer step writes
+    unsigned int *done;        // device counter: blocks finished in this launch
     double *wave;
     const double *w_row;
     ObsDev obs;
 };
 
-// Partial bilinear sample (Sec. "waveform extraction" of the design notes):
-// slot 0 holds (1 - fr) * [(1-fth) w_j0 Phi_{i0,j0} + fth w_j0+1 Phi_{i0,j0+1}],
-// slot 1 the same at column i0 + 1 times fr; the sample is slot 0 + slot 1.
-template <typename T, int K>
-__device__ __forceinline__ void observe(int i, int lane, const T (&o)[4][K], const WaveArgs &wa)
+// After the last inner step of an outer step the last block to finish moves
+// the sample counter on.  Every block reads the counter before it arrives
+// here, so the increment cannot race with a read of the same launch; the next
+// launch on the stream sees it.  Keeping the index on the device lets a
+// captured chunk of launches be replayed unchanged.
+__device__ __forceinline__ void advance_sample(const WaveArgs &wa)
 {
-    for (int k = 0; k < wa.obs.n; ++k) {
-        const int slot = (i == wa.obs.i0[k]) ? 0 : ((i == wa.obs.i0[k] + 1) ? 1 : -1);
-        if (slot < 0) continue;
-        const int j0 = wa.obs.j0[k];
-        const double w0 = (1.0 - wa.obs.ft[k]) * wa.w_row[j0];
-        const double w1 = wa.obs.ft[k] * wa.w_row[j0 + 1];
-        double cr = 0.0, ci = 0.0;
-#pragma unroll
-        for (int t = 0; t < K; ++t) {
-            const int r = lane * K + t;
-            if (r == j0) {
-                cr += w0 * (double)o[0][t];
-                ci += w0 * (double)o[1][t];
-            } else if (r == j0 + 1) {
-                cr += w1 * (double)o[0][t];
-                ci += w1 * (double)o[1][t];
-            }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            cr += __shfl_xor_sync(kFull, cr, off);
-            ci += __shfl_xor_sync(kFull, ci, off);
-        }
-        if (lane == 0) {
-            const double wr = slot ? wa.obs.wr1[k] : wa.obs.wr0[k];
-            double *dst = wa.wave + ((size_t)k * wa.cap + wa.sample) * 4 + 2 * slot;
-            dst[0] = wr * cr;
-            dst[1] = wr * ci;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(wa.done, 1u);
+        if (prev == gridDim.x - 1) {
+            atomicAdd((unsigned long long *)wa.sample, 1ull);
+            atomicExch(wa.done, 0u);
+            __threadfence();
         }
     }
 }
@@ -304,7 +108,7 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
                 full_node<T, K>(hm, hp, ua, node + (size_t)i * NQ + row, en, o);
                 if (i == 0 || i == Nr - 1) zero_col<T, K>(o);
                 store_col<T, K>(u_out + (size_t)i * SP + row, o);
-                if (wa.write) observe<T, K>(i, lane, o, wa);
+                if (wa.write) observe<T, K>(i, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row);
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c)
@@ -336,8 +140,9 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
         full_node<T, K>(hl, hp, ua, node + (size_t)i0 * NQ + row, en, o);
         if (i0 == 0 || i0 == Nr - 1) zero_col<T, K>(o);
         store_col<T, K>(u_out + (size_t)i0 * SP + row, o);
-        if (wa.write) observe<T, K>(i0, lane, o, wa);
+        if (wa.write) observe<T, K>(i0, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row);
     }
+    if (wa.write) advance_sample(wa);
 }
 
 template <typename T, int K>
@@ -345,7 +150,8 @@ cudaError_t launch_typed(const StepLaunch &L, cudaStream_t st)
 {
     WaveArgs wa;
     wa.write = L.write_wave;
-    wa.sample = L.sample;
+    wa.sample = L.sample_ctr;
+    wa.done = L.done_ctr;
     wa.cap = L.wave_cap;
     wa.wave = L.wave;
     wa.w_row = L.w_row;
@@ -382,6 +188,8 @@ int step_grid_blocks(int precision, int K, int Nr, int num_sms)
     int blocks = num_sms * per_sm;
     const int max_blocks = Nr / (2 * W);
     if (blocks > max_blocks) blocks = max_blocks;
+    // whole waves only: a partial wave leaves some SMs with twice the work
+    if (blocks > num_sms) blocks = (blocks / num_sms) * num_sms;
     return blocks < 1 ? 1 : blocks;
 }
 
