@@ -15,7 +15,7 @@
 // The half-step planes of the paper's OpenCL code never exist in memory.  The
 // theta-pole boundary conditions are folded into the coefficient tables, so
 // the arithmetic is branch-free: 28 FP64 (or FP32) operations per half node
-// and 28 per node.  A segment recomputes one half node at its left end.
+// and 28 per node.
 #include "tk_stencil.cuh"
 
 namespace tk {
@@ -50,9 +50,10 @@ __device__ __forceinline__ void advance_sample(const WaveArgs &wa)
     }
 }
 
-// Work split: the grid has exactly (SMs x resident blocks) blocks of
-// kStepWarps warps; global warp g owns columns [g Nr / G, (g+1) Nr / G), so
-// every SM gets the same number of columns to within one per warp.  A warp
+// Work split: the grid is one wave of resident blocks (SMs x blocks per SM)
+// of kStepThreads/32 warps, or fewer on a small grid (at least one column per
+// warp); global warp g of G owns columns [g Nr / G, (g+1) Nr / G), so every
+// SM gets the same number of columns to within one per warp.  A warp
 // needs the half-step value at the left edge of its range; the first warp of
 // a block recomputes it, every other warp receives it from its left
 // neighbour through shared memory once both have finished their sweep (the
@@ -176,7 +177,6 @@ int resident_blocks()
 
 int step_grid_blocks(int precision, int K, int Nr, int num_sms)
 {
-    // one wave of resident blocks, each warp at least two columns wide
     int per_sm = 1;
     if (precision == 0)
         per_sm = K == 1 ? resident_blocks<double, 1>() : K == 2 ? resident_blocks<double, 2>()
@@ -184,12 +184,13 @@ int step_grid_blocks(int precision, int K, int Nr, int num_sms)
     else
         per_sm = K == 1 ? resident_blocks<float, 1>() : K == 2 ? resident_blocks<float, 2>()
                                                                : resident_blocks<float, 4>();
+    // One wave of resident blocks (a multiple of the SM count) when the grid
+    // is large; for a small grid, as many warps as columns, since there every
+    // warp's sweep is latency-bound and shorter sweeps finish sooner.
     const int W = kStepThreads / 32;
     int blocks = num_sms * per_sm;
-    const int max_blocks = Nr / (2 * W);
+    const int max_blocks = Nr / W;   // every warp keeps at least one column
     if (blocks > max_blocks) blocks = max_blocks;
-    // whole waves only: a partial wave leaves some SMs with twice the work
-    if (blocks > num_sms) blocks = (blocks / num_sms) * num_sms;
     return blocks < 1 ? 1 : blocks;
 }
 
