@@ -132,6 +132,25 @@ tk_status tk_set_graph_chunk(tk_solver *S, int outer_steps);
 tk_status tk_extract(tk_solver *S, int obs_id, double *re, double *im, int capacity, int *count,
                      int on_device);
 
+/* Allocation-free read-out of a waveform into host memory (the paper has no
+ * counterpart; it is for callers that must not allocate device memory, such
+ * as code running while a CUDA graph is being captured, loops whose memory is
+ * fixed in advance, or hosts that route all device memory through their own
+ * pool -- tk_extract allocates a temporary device buffer on every call).
+ * Copies samples [first, first + count) of observer obs_id to re[0..count)
+ * and im[0..count) (host pointers, pageable or pinned) and synchronizes the
+ * solver's stream.  Device work goes through a 1 MiB array compiled into the
+ * library, so count is limited to 65536 per call (TK_ERR_ARG beyond; read a
+ * longer waveform in pieces).  The array is shared by every call in the
+ * process and keeps the last call's contents: calls whose work overlaps on
+ * the GPU (other threads, other streams) race on it and must be serialized
+ * by the caller.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Allocates nothing: no cudaMalloc, cudaFree or allocating library
+ * call. */
+tk_status tk_extract_noalloc(tk_solver *S, int obs_id, int first, int count, double *re,
+                             double *im);
+
 /* Current state as planes4 (4 * Ntheta * Nr doubles), host or device. */
 tk_status tk_get_state(tk_solver *S, double *planes4, int on_device);
 

@@ -30,7 +30,8 @@ EXPORTS = ("tk_make_grid", "tk_precompute_coeffs", "tk_set_initial_data", "tk_ad
            "tk_step", "tk_extract", "tk_get_state", "tk_set_state", "tk_stability_bound", "tk_steps_done",
            "tk_check_finite", "tk_synchronize", "tk_last_error", "tk_destroy", "tk_set_graph_chunk",
            "tk_batch_create", "tk_batch_step", "tk_batch_tune", "tk_batch_set_segment",
-           "tk_batch_set_graph_chunk", "tk_batch_info", "tk_batch_last_error", "tk_batch_destroy")
+           "tk_batch_set_graph_chunk", "tk_batch_info", "tk_batch_last_error", "tk_batch_destroy",
+           "tk_extract_noalloc")
 
 
 class TkError(RuntimeError):
@@ -79,6 +80,7 @@ def load_library(path: str = LIB_PATH):
             "tk_batch_info": (C.c_int, [_vp, _ip, _ip, _ip]),
             "tk_batch_last_error": (C.c_char_p, [_vp]),
             "tk_batch_destroy": (None, [_vp]),
+            "tk_extract_noalloc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)

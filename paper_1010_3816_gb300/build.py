@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtk.so")
-SOURCES = ["tk_api.cu", "tk_coeffs.cu", "tk_step.cu", "tk_layout.cu", "tk_batch.cu"]
+SOURCES = ["tk_api.cu", "tk_coeffs.cu", "tk_step.cu", "tk_layout.cu", "tk_batch.cu",
+           "tk_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
