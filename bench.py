@@ -36,9 +36,11 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
-from inputs import KERR_25601x64, SCHWARZSCHILD_1601x32, initial_planes  # noqa: E402
+from inputs import (ADJOINT_16001x128, KERR_25601x64, SCHWARZSCHILD_1601x32,  # noqa: E402
+                    adjoint_target_params, batched_instances, initial_planes)
 
-WORKLOADS = {"kerr": KERR_25601x64, "schwarzschild": SCHWARZSCHILD_1601x32}
+WORKLOADS = {"kerr": KERR_25601x64, "schwarzschild": SCHWARZSCHILD_1601x32,
+             "batched": None, "adjoint": ADJOINT_16001x128}
 
 # FP64 work of the step kernel per grid-point update, counted from its source:
 # half node (Eq. lw1) 4 adds + 4 multiplies + 20 FMAs, node (Eq. lw2) 4 adds +
@@ -193,6 +195,205 @@ def _config(w, args, world):
                 w.points * TABLE_BYTES_PER_UPDATE[args.precision] / 1e6)}
 
 
+def _clock_checked(clk):
+    bad = [r for r in clk.get("reasons", []) if r in ("hw_slowdown", "hw_thermal_slowdown",
+                                                      "sw_thermal_slowdown")]
+    return bad
+
+
+def run_batched(args, tk, torch, rank, world, local):
+    """The 24-instance batch: instances sharded across ranks by cost, each
+    rank's share advanced by one tk_batch (one launch per inner tick, graph
+    replay, autotuned segment length); compared with running the same
+    instances one after another through tk_step."""
+    from paper_1010_3816_gb300 import distributed as D
+    inst_all = batched_instances()
+    n_outer = args.outer_steps or 500
+    mine = D.shard([w.points * w.substeps for w in inst_all], rank, world)
+    inst = [inst_all[k] for k in mine]
+    stream = torch.cuda.current_stream()
+    solvers, planes, outs = [], [], []
+    for w in inst:
+        g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
+                      substeps=w.substeps, variable=w.variable, stream=stream.cuda_stream)
+        g.precompute(w.a, w.M, w.s, w.m)
+        re, im = initial_planes(w)
+        d = (torch.from_numpy(re).cuda(), torch.from_numpy(im).cuda())
+        g.set_initial(*d)
+        ids = [g.add_observer(r, t) for r, t in w.observers]
+        outs.append([(k, torch.empty(n_outer, dtype=torch.float64, device="cuda"),
+                      torch.empty(n_outer, dtype=torch.float64, device="cuda")) for k in ids])
+        solvers.append(g)
+        planes.append(d)
+    batch = tk.Batch(solvers)
+    seg, tuned_ms = batch.tune(3)
+    info = batch.info()
+    updates = sum(w.points * w.substeps for w in inst) * n_outer
+    ev = []
+
+    def solve(record, batched=True):
+        for g, w, d in zip(solvers, inst, planes):
+            tk.tk_precompute_coeffs(g.h, w.a, w.M, w.s, w.m)
+            tk.tk_set_initial_data(g.h, *d)
+        if record:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        if batched:
+            batch.step(n_outer)
+        else:
+            for g in solvers:
+                g.step(n_outer)
+        if record:
+            e1.record(stream)
+            ev.append((e0, e1))
+        for g, o in zip(solvers, outs):
+            for k, a, b in o:
+                tk.tk_extract(g.h, k, a, b)
+
+    for _ in range(args.warmup):
+        solve(False)
+    torch.cuda.synchronize()
+    D.barrier()
+    clocks = ClockSampler(_gpu_id(torch, local))
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        solve(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    D.barrier()
+    clk = clocks.stop()
+    ms = D.reduce_max(t0.elapsed_time(t1), device="cuda")
+    total_updates = D.reduce_sum(updates, device="cuda")
+    value = total_updates * args.steps / (ms * 1e-3)
+    kern_s = statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e-3
+    # the same instances through tk_step, one after another
+    solve(False, batched=False)
+    torch.cuda.synchronize()
+    p0 = torch.cuda.Event(enable_timing=True)
+    p1 = torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    solve(True, batched=False)
+    p1.record(stream)
+    torch.cuda.synchronize()
+    plain = updates / (p0.elapsed_time(p1) * 1e-3)
+    f_clk = (clk.get("sm_mhz") or 2070.0) * 1e6
+    achieved = FP64_FLOP_PER_UPDATE * updates / kern_s / 1e12
+    peak = NUM_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * f_clk / 1e12
+    if rank == 0:
+        line = {
+            "metric": "grid-point updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "batched_24_instances", "instances": len(inst_all),
+                       "instances_on_rank0": len(inst), "outer_steps": n_outer,
+                       "outer_steps_of_full_run": inst_all[0].steps,
+                       "substeps_by_Ntheta": {"32": 2, "64": 4, "128": 8}, "ticks_per_outer_step": info["kmax"],
+                       "segment_autotuned": seg, "tuned_ms_per_outer_step": tuned_ms,
+                       "grid_blocks": info["blocks"],
+                       "parallelism": f"instances sharded over {world} GPUs" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "batch_step_kernel<double>",
+                         "peak_source": "152 SMs x 2 DFMA/clk (measured) x 2 flop x median SM clock"},
+            "plain_tk_step": {"value": plain, "unit": "updates/s",
+                              "batched_over_plain": (updates / kern_s) / plain},
+            "cpu_baseline": None, "e2e": None, "clocks": clk,
+            "gpu_launches": args.steps * (n_outer * info["kmax"] + 3 * len(inst) +
+                                          sum(len(o) for o in outs)),
+        }
+        print(json.dumps(line))
+    batch.close()
+    return 0
+
+
+def run_adjoint(args, tk, torch, rank, world, local):
+    """Gradient of the waveform misfit sum_t |W(t) - W_target(t)|^2 with
+    respect to the amplitude, centre and width of the initial pulse: forward
+    solve, then the adjoint sweep (tk_adjoint) through torch.autograd."""
+    w = ADJOINT_16001x128
+    n_outer = args.outer_steps or 2000
+    stream = torch.cuda.current_stream()
+    g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
+                  substeps=w.substeps, variable=w.variable, stream=stream.cuda_stream)
+    g.precompute(w.a, w.M, w.s, w.m)
+    g.set_initial(*(torch.zeros((w.Ntheta, w.Nr), dtype=torch.float64, device="cuda") for _ in range(2)))
+    for r, t in w.observers:
+        g.add_observer(r, t)
+    rs = torch.tensor(w.rs_min + np.arange(w.Nr) * w.drs, dtype=torch.float64, device="cuda")
+    th = torch.tensor((np.arange(w.Ntheta) + 0.5) * (math.pi / w.Ntheta), dtype=torch.float64,
+                      device="cuda")
+    ang = (torch.sin(th) ** 2)[:, None]
+
+    def planes(A, c, s):
+        G = A * torch.exp(-((rs - c) ** 2) / (2.0 * s ** 2))
+        re = ang * G[None, :]
+        return re, torch.zeros_like(re)
+
+    with torch.no_grad():
+        tA, tc, tw = (torch.tensor(v, dtype=torch.float64, device="cuda") for v in adjoint_target_params())
+        target = tk.waveforms(g, *planes(tA, tc, tw), n_outer).clone()
+    ev_f, ev_b = [], []
+
+    def gradient(record):
+        p = [torch.tensor(v, dtype=torch.float64, device="cuda", requires_grad=True)
+             for v in (w.amp, w.center, w.width)]
+        if record:
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            e[0].record(stream)
+        W = tk.waveforms(g, *planes(*p), n_outer)
+        L = ((W - target) ** 2).sum()
+        if record:
+            e[1].record(stream)
+        L.backward()
+        if record:
+            e[2].record(stream)
+            ev_f.append((e[0], e[1]))
+            ev_b.append((e[1], e[2]))
+        return [x.grad for x in p]
+
+    for _ in range(args.warmup):
+        gradient(False)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(_gpu_id(torch, local))
+    clocks.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        grads = gradient(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    inner = w.points * w.substeps * n_outer
+    value = 2 * inner * args.steps / (ms * 1e-3)
+    fwd = statistics.mean(a.elapsed_time(b) for a, b in ev_f) * 1e-3
+    bwd = statistics.mean(a.elapsed_time(b) for a, b in ev_b) * 1e-3
+    if rank == 0:
+        line = {
+            "metric": "grid-point updates/s (forward + adjoint)", "value": value, "unit": "updates/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "Nr": w.Nr, "Ntheta": w.Ntheta, "a": w.a,
+                       "outer_steps": n_outer, "outer_steps_of_full_run": w.steps,
+                       "substeps": w.substeps, "loss": "sum_t |W(t) - W_target(t)|^2 at (400, pi/2)",
+                       "gradient_wrt": ["amplitude", "centre", "width", "initial planes"],
+                       "parallelism": "single GPU", "l2": "inputs larger than L2"},
+            "forward_updates_per_s": inner / fwd, "adjoint_updates_per_s": inner / bwd,
+            "grad": [float(x) for x in grads],
+            "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
+            "gpu_launches": args.steps * 2 * (n_outer * w.substeps),
+        }
+        print(json.dumps(line))
+    g.close()
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,7 +412,7 @@ def main() -> int:
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if args.impl == "reference":
-        return run_reference(args, w)
+        return run_reference(args, w or batched_instances()[2])
 
     import torch
     import paper_1010_3816_gb300 as tk
@@ -223,6 +424,12 @@ def main() -> int:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     tk.load_library()
+    if args.workload in ("batched", "adjoint"):
+        fn = run_batched if args.workload == "batched" else run_adjoint
+        rc = fn(args, tk, torch, rank, world, local)
+        if dist:
+            dist.destroy_process_group()
+        return rc
     n_outer = args.outer_steps or w.steps
     updates = w.points * n_outer * w.substeps
     launches_per_solve = 3 + n_outer * w.substeps + len(w.observers)

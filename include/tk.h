@@ -151,6 +151,26 @@ tk_status tk_extract(tk_solver *S, int obs_id, double *re, double *im, int capac
 tk_status tk_extract_noalloc(tk_solver *S, int obs_id, int first, int count, double *re,
                              double *im);
 
+/* Gradient of a loss with respect to the initial data, by the transposed
+ * Lax-Wendroff step run backward over the steps taken since
+ * tk_set_initial_data.  The step of Eqs. (lw1)/(lw2) is linear and
+ * time-invariant, so the backward sweep needs no stored trajectory: only the
+ * loss gradients.
+ *   dL_dwave   [nobs][count][2]: dL/d(Re W), dL/d(Im W) for every sample of
+ *              every observer (count = outer steps taken), or NULL
+ *   dL_dfinal  planes4: dL/d(final state), or NULL (not both NULL)
+ *   on_device  location of dL_dwave / dL_dfinal
+ *   grad       output: with independent_pi = 0, two planes [Ntheta][Nr],
+ *              dL/d(phi_re), dL/d(phi_im) of tk_set_initial_data with the
+ *              momentum derived from Phi (pi planes NULL); with
+ *              independent_pi = 1, planes4 including dL/d(pi planes)
+ *   grad_on_device location of grad
+ * The solver's state is not touched.  Allocates two adjoint state levels on
+ * first use (kept until tk_destroy) and temporary buffers for host inputs.
+ * Synchronizes the stream when an input or the output is in host memory. */
+tk_status tk_adjoint(tk_solver *S, const double *dL_dwave, const double *dL_dfinal, int on_device,
+                     double *grad, int grad_on_device, int independent_pi);
+
 /* Current state as planes4 (4 * Ntheta * Nr doubles), host or device. */
 tk_status tk_get_state(tk_solver *S, double *planes4, int on_device);
 

@@ -124,11 +124,18 @@ KERR_25601x64 = Workload(
     observers=((500.0, math.pi / 4), (500.0, math.pi / 2)))
 
 
+# Lax-Wendroff steps per outer step of the batched instances, by Ntheta: the
+# angular stiffness grows like Ntheta^2, and k keeps the growth factor of the
+# stiffest angular mode over 5000 outer steps of dt = 1/32 near e.
+BATCH_SUBSTEPS = {32: 2, 64: 4, 128: 8}
+
+
 def batched_instances(seed: int = 2) -> List[Workload]:
     """24 independent solves: a in {0, .5, .9, .99} x m in {0,1,2,3,4,-2}, s = -2,
     dr* = 1/16, Nr and Ntheta cycling through {4001, 8001, 16001} and
     {32, 64, 128}, centre ~ U[10, 60), width ~ U[2, 8) from SplitMix64(seed),
-    5000 outer steps of dt = 1/32, observer at (r*_max - 50, pi/2)."""
+    5000 outer steps of dt = 1/32 (BATCH_SUBSTEPS inner steps each), observer
+    at (r*_max - 50, pi/2)."""
     avals = (0.0, 0.5, 0.9, 0.99)
     mvals = (0, 1, 2, 3, 4, -2)
     nrs = (4001, 8001, 16001)
@@ -146,7 +153,27 @@ def batched_instances(seed: int = 2) -> List[Workload]:
             width = 2.0 + 6.0 * u[2 * k + 1]
             out.append(Workload(name=f"batch_a{a}_m{m}_{Nr}x{Nth}", a=a, m=m, rs_min=rs_min,
                                 rs_max=rs_max, Nr=Nr, Ntheta=Nth, dt=1.0 / 32.0, steps=5000,
+                                substeps=BATCH_SUBSTEPS[Nth],
                                 center=float(center), width=float(width),
                                 observers=((rs_max - 50.0, math.pi / 2),)))
             k += 1
     return out
+
+
+# Adjoint workload: Kerr a = 0.7, 16001 x 128, dr* = 1/16, 20000 outer steps of
+# dt = 1/32 (8 Lax-Wendroff steps each), observer at (400, pi/2); the target
+# waveform comes from a Gaussian whose amplitude, centre and width are
+# perturbed by SplitMix64(seed 4) draws.
+ADJOINT_16001x128 = Workload(
+    name="adjoint_kerr_a0.7_16001x128_20000steps", a=0.7, rs_min=-100.0, rs_max=900.0,
+    Nr=16001, Ntheta=128, dt=1.0 / 32.0, substeps=8, steps=20000, center=50.0, width=6.0,
+    observers=((400.0, math.pi / 2),))
+
+
+def adjoint_target_params(seed: int = 4):
+    """(amplitude, centre, width) of the target pulse: the workload's values
+    times 1 + U[-5%, 5%) each."""
+    u = uniform01(seed, 3)
+    w = ADJOINT_16001x128
+    f = 1.0 + 0.1 * (u - 0.5)
+    return w.amp * f[0], w.center * f[1], w.width * f[2]

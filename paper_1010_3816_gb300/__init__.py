@@ -31,7 +31,7 @@ EXPORTS = ("tk_make_grid", "tk_precompute_coeffs", "tk_set_initial_data", "tk_ad
            "tk_check_finite", "tk_synchronize", "tk_last_error", "tk_destroy", "tk_set_graph_chunk",
            "tk_batch_create", "tk_batch_step", "tk_batch_tune", "tk_batch_set_segment",
            "tk_batch_set_graph_chunk", "tk_batch_info", "tk_batch_last_error", "tk_batch_destroy",
-           "tk_extract_noalloc")
+           "tk_extract_noalloc", "tk_adjoint")
 
 
 class TkError(RuntimeError):
@@ -81,6 +81,7 @@ def load_library(path: str = LIB_PATH):
             "tk_batch_last_error": (C.c_char_p, [_vp]),
             "tk_batch_destroy": (None, [_vp]),
             "tk_extract_noalloc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
+            "tk_adjoint": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, C.c_int, C.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -209,6 +210,20 @@ def tk_stability_bound(h, growth_per_step: float = 2.5e-5):
     return d.value, k.value
 
 
+def tk_adjoint(h, grad, dL_dwave=None, dL_dfinal=None, independent_pi: bool = False) -> None:
+    """dL/d(initial data) into ``grad`` (numpy array or CUDA tensor of 2 or 4
+    planes [Ntheta][Nr]); dL_dwave is [nobs][count][2], dL_dfinal planes4."""
+    pw, dw, kw = _arg(dL_dwave)
+    pf, df, kf = _arg(dL_dfinal)
+    locs = {d for d in (dw, df) if d is not None}
+    if len(locs) != 1:
+        raise ValueError("give dL_dwave and/or dL_dfinal, both on the host or both on the device")
+    pg, dg, kg = _arg(grad)
+    _check(h, load_library().tk_adjoint(h, pw, pf, locs.pop(), pg, dg, 1 if independent_pi else 0))
+    if dg == 0 and isinstance(grad, np.ndarray) and kg is not grad:
+        grad[...] = kg
+
+
 def tk_steps_done(h) -> int:
     v = C.c_int64(0)
     _check(h, load_library().tk_steps_done(h, C.byref(v)))
@@ -312,7 +327,9 @@ class Solver:
         return self
 
     def add_observer(self, rstar, theta) -> int:
-        return tk_add_observer(self.h, rstar, theta)
+        k = tk_add_observer(self.h, rstar, theta)
+        self._observers = getattr(self, "_observers", []) + [(rstar, theta)]
+        return k
 
     def step(self, n: int):
         tk_step(self.h, n)
@@ -333,6 +350,10 @@ class Solver:
 
     def stability_bound(self, growth_per_step: float = 2.5e-5):
         return tk_stability_bound(self.h, growth_per_step)
+
+    def adjoint(self, grad, dL_dwave=None, dL_dfinal=None, independent_pi=False):
+        tk_adjoint(self.h, grad, dL_dwave, dL_dfinal, independent_pi)
+        return grad
 
     def steps_done(self) -> int:
         return tk_steps_done(self.h)
@@ -378,3 +399,34 @@ class Batch:
 
     def info(self):
         return tk_batch_info(self.b)
+
+
+def waveforms(solver: "Solver", phi_re, phi_im, n_steps: int):
+    """Differentiable map from the initial planes (CUDA float64 tensors
+    [Ntheta][Nr], momentum for zero time derivative) to the waveforms of the
+    solver's observers, a tensor [nobs, n_steps, 2] (real, imaginary).  The
+    solver must be precomputed and have its observers; its state is
+    overwritten.  The backward pass runs the adjoint kernel (tk_adjoint)."""
+    import torch
+
+    class _Waveforms(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, pr, pi):
+            solver.set_initial(pr.detach().contiguous(), pi.detach().contiguous())
+            solver.step(n_steps)
+            nobs = len(solver._observers) if hasattr(solver, "_observers") else None
+            out = []
+            for k in range(nobs):
+                re = torch.empty(n_steps, dtype=torch.float64, device=pr.device)
+                im = torch.empty(n_steps, dtype=torch.float64, device=pr.device)
+                tk_extract(solver.h, k, re, im)
+                out.append(torch.stack([re, im], dim=1))
+            return torch.stack(out, dim=0)
+
+        @staticmethod
+        def backward(ctx, g):
+            grad = torch.empty((2, solver.Ntheta, solver.Nr), dtype=torch.float64, device=g.device)
+            tk_adjoint(solver.h, grad, dL_dwave=g.detach().contiguous())
+            return grad[0], grad[1]
+
+    return _Waveforms.apply(phi_re, phi_im)

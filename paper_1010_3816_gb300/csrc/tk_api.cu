@@ -45,7 +45,8 @@ tk_status alloc(tk_solver *S, void **p, size_t bytes)
 void release(tk_solver *S)
 {
     void *ptrs[] = {S->u[0], S->u[1], S->half, S->node, S->b_node, S->w_row,
-                    S->x_node, S->x_half, S->ang, S->staging, S->flag, S->stiff, S->ctr, S->wave};
+                    S->x_node, S->x_half, S->ang, S->staging, S->flag, S->stiff, S->ctr, S->wave,
+                    S->adj[0], S->adj[1]};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < 2; ++k)

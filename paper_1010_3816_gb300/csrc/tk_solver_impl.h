@@ -25,6 +25,7 @@ struct tk_solver {
     int *flag = nullptr;
     unsigned long long *stiff = nullptr;  // [max omega^2, max b] as double bit patterns
     long long *ctr = nullptr;   // [0]: sample index of the next outer step, [1]: blocks done
+    void *adj[2] = {nullptr, nullptr};  // adjoint state levels (tk_adjoint), allocated on use
     // physics
     tk::Kerr kerr{};
     bool have_coeffs = false, have_state = false;
