@@ -18,7 +18,7 @@ constexpr int kMaxObservers = 16;
 constexpr int kMaxK = 4;          // theta rows per lane: Ntheta <= 32 * kMaxK
 constexpr int kNCH = 11;          // half-node table entries
 constexpr int kNCN = 10;          // node table entries
-constexpr int kStepThreads = 128; // threads per block of the step kernel
+constexpr int kStepThreads = 256; // threads per block of the step kernel (8 warps)
 
 // Half-node table entries (Eq. lw1 with dtau = dt/2, rho = 1/dr*):
 //   HP  = 1/2 + dtau rho b        coefficient of Phi_i   in Phi^{n+1/2}

@@ -50,14 +50,42 @@ __device__ __forceinline__ void advance_sample(const WaveArgs &wa)
     }
 }
 
-// Work split: the grid is one wave of resident blocks (SMs x blocks per SM)
-// of kStepThreads/32 warps, or fewer on a small grid (at least one column per
-// warp); global warp g of G owns columns [g Nr / G, (g+1) Nr / G), so every
-// SM gets the same number of columns to within one per warp.  A warp
+// Work split: the grid is one wave of resident blocks (SMs x blocks per SM),
+// or fewer on a small grid (at least one column per warp).  Block b owns
+// columns [b Nr / B, (b+1) Nr / B), within which its warps take contiguous
+// ranges.  Warps w and w + 4 run on the same SM sub-partition, so the four
+// quarters of the block's columns go to the four pairs and each pair splits
+// its quarter in two: every sub-partition gets the same number of columns to
+// within one, and the extra column of a pair costs no idle pipe.  A warp
 // needs the half-step value at the left edge of its range; the first warp of
 // a block recomputes it, every other warp receives it from its left
 // neighbour through shared memory once both have finished their sweep (the
 // warp's first node is deferred until then).
+// Also returns the nearest warp to the left in the block that owns columns
+// (-1 if none: this warp then recomputes its left half-step value itself).
+__device__ __forceinline__ void warp_range(int Nr, int wib, int *i0, int *i1, int *left)
+{
+    constexpr int W = kStepThreads / 32;
+    const long long B = gridDim.x, b = blockIdx.x;
+    const int b0 = (int)((b * Nr) / B), b1 = (int)(((b + 1) * Nr) / B);
+    const int C = b1 - b0;
+    int start = b0, cnt = 0, prev = -1;
+    for (int w = 0; w <= wib; ++w) {
+        const int p = w % (W / 2);
+        const int cp = (int)(((long long)(p + 1) * C) / (W / 2) - ((long long)p * C) / (W / 2));
+        const int c = (w < W / 2) ? (cp + 1) / 2 : cp / 2;
+        if (w < wib) {
+            start += c;
+            if (c > 0) prev = w;
+        } else {
+            cnt = c;
+        }
+    }
+    *i0 = start;
+    *i1 = start + cnt;
+    *left = prev;
+}
+
 template <typename T, int K>
 __global__ void __launch_bounds__(kStepThreads)
 lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__restrict__ half,
@@ -65,18 +93,16 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
 {
     constexpr int NP = 32 * K;
     constexpr size_t SP = 4 * NP, HP = (size_t)kNCH * NP, NQ = (size_t)kNCN * NP;
-    constexpr int W = kStepThreads / 32;
     // per warp: [0] its last half node (read by the right neighbour),
     //           [1] u^n at its first column, [2] u^{n+1/2} right of its first column
-    __shared__ T sh[W][3][4][NP];
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    T(*sh)[3][4][NP] = reinterpret_cast<T(*)[3][4][NP]>(sh_raw);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const long long G = (long long)gridDim.x * W;
-    const long long g = (long long)blockIdx.x * W + wib;
-    const int i0 = (int)((g * Nr) / G);
-    const int i1 = (int)(((g + 1) * Nr) / G);
+    int i0, i1, left;
+    warp_range(Nr, wib, &i0, &i1, &left);
     const int row = lane * K;
-    const bool lead = (wib == 0);
+    const bool lead = (left < 0);
 
     T ua[4][K], hm[4][K];
     if (i1 > i0) {
@@ -134,7 +160,7 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
         for (int c = 0; c < 4; ++c)
 #pragma unroll
             for (int t = 0; t < K; ++t) {
-                hl[c][t] = sh[wib - 1][0][c][row + t];
+                hl[c][t] = sh[left][0][c][row + t];
                 ua[c][t] = sh[wib][1][c][row + t];
                 hp[c][t] = sh[wib][2][c][row + t];
             }
@@ -144,6 +170,22 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
         if (wa.write) observe<T, K>(i0, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row);
     }
     if (wa.write) advance_sample(wa);
+}
+
+template <typename T, int K>
+constexpr size_t step_smem_bytes()
+{
+    return (size_t)(kStepThreads / 32) * 3 * 4 * 32 * K * sizeof(T);
+}
+
+// Opt the kernel in to its dynamic shared memory once (above 48 KB for K = 4).
+template <typename T, int K>
+cudaError_t step_smem_setup()
+{
+    static cudaError_t e = cudaFuncSetAttribute(lw_step_kernel<T, K>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)step_smem_bytes<T, K>());
+    return e;
 }
 
 template <typename T, int K>
@@ -157,7 +199,9 @@ cudaError_t launch_typed(const StepLaunch &L, cudaStream_t st)
     wa.wave = L.wave;
     wa.w_row = L.w_row;
     wa.obs = L.obs;
-    lw_step_kernel<T, K><<<L.blocks, kStepThreads, 0, st>>>(
+    cudaError_t e = step_smem_setup<T, K>();
+    if (e != cudaSuccess) return e;
+    lw_step_kernel<T, K><<<L.blocks, kStepThreads, step_smem_bytes<T, K>(), st>>>(
         (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node, L.Nr,
         (T)(0.25 * L.dt_inner), (T)(0.5 * L.dt_inner), wa);
     return cudaGetLastError();
@@ -167,8 +211,9 @@ template <typename T, int K>
 int resident_blocks()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_step_kernel<T, K>, kStepThreads, 0) !=
-        cudaSuccess)
+    if (step_smem_setup<T, K>() != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_step_kernel<T, K>, kStepThreads,
+                                                      step_smem_bytes<T, K>()) != cudaSuccess)
         n = 1;
     return n < 1 ? 1 : n;
 }

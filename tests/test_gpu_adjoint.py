@@ -160,3 +160,22 @@ def test_gaussian_parameter_gradients_match_finite_differences():
         fd = (Lp - Lm) / (2 * h)
         assert abs(fd - grads[k]) <= 1e-6 * max(abs(fd), 1e-12), (k, fd, grads[k])
     g.close()
+
+
+def test_dot_product_full_size_adjoint_grid():
+    """The 16001 x 128 Kerr a = 0.7 grid of the adjoint workload (k = 8), 15
+    outer steps: <g, J u> = <J^T g, u>."""
+    from inputs import ADJOINT_16001x128
+    w = ADJOINT_16001x128.with_(steps=15, observers=((20.0, math.pi / 2), (40.0, 1.0)))
+    g = _solver(w)
+    u0 = _edge0(_rand((2, w.Ntheta, w.Nr), 31))
+    dwave = _rand((len(w.observers), w.steps, 2), 32)
+    dfin = _rand((4, w.Ntheta, w.Nr), 33)
+    waves, final, _ = _forward(g, w, u0)
+    grad = np.zeros((2, w.Ntheta, w.Nr))
+    g.adjoint(grad, dL_dwave=dwave, dL_dfinal=dfin)
+    lhs = float(np.sum(dwave * waves) + np.sum(dfin * final))
+    rhs = float(np.sum(grad * u0))
+    scale = float(np.sum(np.abs(dwave * waves)) + np.sum(np.abs(dfin * final)))
+    assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
+    g.close()

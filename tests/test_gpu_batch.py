@@ -118,3 +118,25 @@ def test_batch_rejects_mismatched_members():
     g2, _ = _solver(MEMBERS[1].with_(dt=DT / 2))
     with pytest.raises(tk.TkError):
         tk.Batch([g1, g2])
+
+
+def test_full_batched_set_is_bit_identical_to_members_alone():
+    """All 24 instances of the batched workload at full size (16x spread in
+    size, three theta packings, k = 2, 4, 8) for 12 outer steps, in the
+    launch configuration the benchmark times (autotuned segment, graph)."""
+    import paper_1010_3816_gb300 as tk
+    from inputs import batched_instances
+    inst = batched_instances()
+    alone = [_solver(w) for w in inst]
+    for g, _ in alone:
+        g.step(12)
+    ref = _results(alone)
+    for g, _ in alone:
+        g.close()
+    batched = [_solver(w) for w in inst]
+    b = tk.Batch([g for g, _ in batched])
+    assert b.info()["kmax"] == 8
+    b.tune(2)
+    b.step(12)
+    _same(_results(batched), ref)
+    b.close()
