@@ -73,8 +73,10 @@ enum {
  *   rstar_min < rstar_max   radial extent (tortoise coordinate, units of M)
  *   Nr >= 3, 2 <= Ntheta <= 128
  *   dt > 0                  outer time step: one waveform sample per outer step
- *   substeps >= 1           Lax-Wendroff steps per outer step (each dt/substeps);
- *                           0 means 1
+ *   substeps >= 0           Lax-Wendroff steps per outer step (each dt/substeps);
+ *                           0: chosen by every tk_precompute_coeffs as the
+ *                           tk_stability_bound count for a growth of 2.5e-5
+ *                           per step (read it back with tk_get_substeps)
  *   angular_variable        TK_VAR_LITERAL or TK_VAR_REGULARISED
  *   precision               TK_PREC_F64 or TK_PREC_F32
  *   cuda_stream             cudaStream_t to run on (NULL: the legacy default stream)
@@ -102,6 +104,20 @@ tk_status tk_precompute_coeffs(tk_solver *S, double a, double M, int s, int m);
  * pointers, 0 if host.  Resets the step counter and every observer. */
 tk_status tk_set_initial_data(tk_solver *S, const double *phi_re, const double *phi_im,
                               const double *pi_re, const double *pi_im, int on_device);
+
+/* Initial data generated on the device (the synthetic pulses of the
+ * benchmarks): the evolved field's real plane is
+ *   amp * exp(-(r*_i - center)^2 / (2 width^2)) * sin^2(theta_j) + noise_amp * (2 u - 1)
+ * and its imaginary plane noise_amp * (2 u' - 1), where u and u' are uniform
+ * doubles in [0, 1) from SplitMix64 (Steele, Lea and Flood, OOPSLA 2014) with
+ * this seed: output j*Nr + i for u and Nr*Ntheta + j*Nr + i for u', each the
+ * top 53 bits of the 64-bit output times 2^-53.  In the regularised variable
+ * this sets Phi^ (so Phi = w(theta) * Phi^).  The momentum is that of zero time
+ * derivative, as for tk_set_initial_data with NULL pi planes.  width > 0,
+ * noise_amp >= 0 (0: no noise), amp and center finite (TK_ERR_ARG otherwise).
+ * Requires tk_precompute_coeffs (TK_ERR_STATE). */
+tk_status tk_set_initial_gaussian(tk_solver *S, double amp, double center, double width,
+                                  double noise_amp, uint64_t seed);
 
 /* Register a waveform observer at (rstar_obs, theta_obs); writes its id.  The
  * sample after every outer step is the bilinear interpolant in (r*, theta) of
@@ -192,6 +208,10 @@ tk_status tk_set_state(tk_solver *S, const double *planes4, int on_device);
  * principal part and is conservative by up to ~2x in dt. */
 tk_status tk_stability_bound(tk_solver *S, double growth_per_step, double *dt_max,
                              int *substeps_needed);
+
+/* Lax-Wendroff steps per outer step in use (the count chosen at the last
+ * tk_precompute_coeffs when the grid was made with substeps = 0). */
+tk_status tk_get_substeps(const tk_solver *S, int *substeps);
 
 /* Outer steps taken since the initial data. */
 tk_status tk_steps_done(const tk_solver *S, int64_t *steps);

@@ -31,7 +31,7 @@ EXPORTS = ("tk_make_grid", "tk_precompute_coeffs", "tk_set_initial_data", "tk_ad
            "tk_check_finite", "tk_synchronize", "tk_last_error", "tk_destroy", "tk_set_graph_chunk",
            "tk_batch_create", "tk_batch_step", "tk_batch_tune", "tk_batch_set_segment",
            "tk_batch_set_graph_chunk", "tk_batch_info", "tk_batch_last_error", "tk_batch_destroy",
-           "tk_extract_noalloc", "tk_adjoint")
+           "tk_extract_noalloc", "tk_adjoint", "tk_set_initial_gaussian", "tk_get_substeps")
 
 
 class TkError(RuntimeError):
@@ -82,6 +82,9 @@ def load_library(path: str = LIB_PATH):
             "tk_batch_destroy": (None, [_vp]),
             "tk_extract_noalloc": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _vp, _vp]),
             "tk_adjoint": (C.c_int, [_vp, _vp, _vp, C.c_int, _vp, C.c_int, C.c_int]),
+            "tk_set_initial_gaussian": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double,
+                                                  C.c_double, C.c_uint64]),
+            "tk_get_substeps": (C.c_int, [_vp, _ip]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -148,6 +151,12 @@ def tk_set_initial_data(h, phi_re, phi_im, pi_re=None, pi_im=None) -> None:
     if len(dev) != 1:
         raise ValueError("all arrays must be on the host or all on the device")
     _check(h, load_library().tk_set_initial_data(h, p[0][0], p[1][0], p[2][0], p[3][0], dev.pop()))
+
+
+def tk_set_initial_gaussian(h, amp: float, center: float, width: float, noise_amp: float = 0.0,
+                            seed: int = 0) -> None:
+    _check(h, load_library().tk_set_initial_gaussian(h, amp, center, width, noise_amp,
+                                                     int(seed) & 0xFFFFFFFFFFFFFFFF))
 
 
 def tk_add_observer(h, rstar_obs: float, theta_obs: float) -> int:
@@ -227,6 +236,12 @@ def tk_adjoint(h, grad, dL_dwave=None, dL_dfinal=None, independent_pi: bool = Fa
 def tk_steps_done(h) -> int:
     v = C.c_int64(0)
     _check(h, load_library().tk_steps_done(h, C.byref(v)))
+    return v.value
+
+
+def tk_get_substeps(h) -> int:
+    v = C.c_int(0)
+    _check(h, load_library().tk_get_substeps(h, C.byref(v)))
     return v.value
 
 
@@ -325,6 +340,14 @@ class Solver:
     def set_initial(self, phi_re, phi_im, pi_re=None, pi_im=None):
         tk_set_initial_data(self.h, phi_re, phi_im, pi_re, pi_im)
         return self
+
+    def set_initial_gaussian(self, amp, center, width, noise=0.0, seed=0):
+        tk_set_initial_gaussian(self.h, amp, center, width, noise, seed)
+        return self
+
+    @property
+    def substeps(self) -> int:
+        return tk_get_substeps(self.h)
 
     def add_observer(self, rstar, theta) -> int:
         k = tk_add_observer(self.h, rstar, theta)

@@ -314,7 +314,33 @@ cudaError_t launch_adjoint_step(int precision, int K, const void *lam, void *mu,
     return launch_adj<float, 4>(lam, mu, half, node, Nr, blocks, dt_in, inj, st);
 }
 
+template <typename T, int K>
+int adj_resident()
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_adjoint_kernel<T, K>, kAdjThreads, 0) !=
+        cudaSuccess)
+        n = 1;
+    return n < 1 ? 1 : n;
+}
+
 }  // namespace
+
+int adjoint_grid_blocks(int precision, int K, int Nr, int num_sms)
+{
+    int per_sm;
+    if (precision == 0)
+        per_sm = K == 1 ? adj_resident<double, 1>() : K == 2 ? adj_resident<double, 2>()
+                                                             : adj_resident<double, 4>();
+    else
+        per_sm = K == 1 ? adj_resident<float, 1>() : K == 2 ? adj_resident<float, 2>()
+                                                            : adj_resident<float, 4>();
+    int blocks = num_sms * per_sm;
+    const int max_blocks = Nr / (kAdjThreads / 32);
+    if (blocks > max_blocks) blocks = max_blocks;
+    return blocks < 1 ? 1 : blocks;
+}
+
 }  // namespace tk
 
 extern "C" tk_status tk_adjoint(tk_solver *S, const double *dL_dwave, const double *dL_dfinal,
@@ -394,7 +420,7 @@ extern "C" tk_status tk_adjoint(tk_solver *S, const double *dL_dwave, const doub
             inj.on = (k == 0) && dwave != nullptr;
             inj.sample = t;
             e = tk::launch_adjoint_step(S->precision, S->K, S->adj[cur], S->adj[cur ^ 1], S->half,
-                                        S->node, S->Nr, S->blocks, dt_in, inj, S->stream);
+                                        S->node, S->Nr, S->adj_blocks, dt_in, inj, S->stream);
             cur ^= 1;
         }
     if (e != cudaSuccess) {

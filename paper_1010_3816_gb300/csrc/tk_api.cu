@@ -100,6 +100,7 @@ void fill_launch(const tk_solver *S, tk::StepLaunch &L)
     L.Nr = S->Nr;
     L.NP = S->NP;
     L.blocks = S->blocks;
+    L.warps = S->warps;
     L.dt_inner = S->dt / S->substeps;
     L.half = S->half;
     L.node = S->node;
@@ -127,6 +128,10 @@ using tkh::state_elems;
 using tkh::enter;
 using tkh::ensure_wave;
 using tkh::fail;
+
+// Tolerated amplification per Lax-Wendroff step of the stiffest angular mode
+// when the solver picks its own number of substeps: a factor e over 40000 steps.
+constexpr double kAutoGrowthPerStep = 2.5e-5;
 
 extern "C" {
 
@@ -163,6 +168,7 @@ tk_status tk_make_grid(tk_solver **out, double rstar_min, double rstar_max, int 
     S->Nth = Ntheta;
     S->K = Ntheta <= 32 ? 1 : (Ntheta <= 64 ? 2 : 4);
     S->NP = 32 * S->K;
+    S->auto_k = (substeps == 0);
     S->substeps = substeps == 0 ? 1 : substeps;
     S->variable = angular_variable;
     S->precision = precision;
@@ -171,7 +177,8 @@ tk_status tk_make_grid(tk_solver **out, double rstar_min, double rstar_max, int 
     S->rs_max = rstar_max;
     S->drs = (rstar_max - rstar_min) / (Nr - 1);
     S->dt = dt;
-    S->blocks = tk::step_grid_blocks(precision, S->K, Nr, S->num_sms);
+    S->blocks = tk::step_grid_shape(precision, S->K, Nr, S->num_sms, &S->warps);
+    S->adj_blocks = tk::adjoint_grid_blocks(precision, S->K, Nr, S->num_sms);
 
     const size_t se = state_elems(S);
     tk_status st = TK_OK;
@@ -218,14 +225,41 @@ tk_status tk_precompute_coeffs(tk_solver *S, double a, double M, int s, int m)
     S->kerr.a = a;
     S->kerr.s = s;
     S->kerr.m = m;
-    const double dt_in = S->dt / S->substeps;
+    if (S->auto_k) S->substeps = 1;
     TK_CUDA(S, tk::launch_invert_tortoise(S->kerr, S->rs_min, S->drs, S->Nr, S->x_node, S->x_half,
                                           S->stream));
-    TK_CUDA(S, tk::launch_coeff_tables(S->kerr, S->variable, S->Nr, S->Nth, S->NP, S->drs, dt_in,
-                                       S->x_node, S->x_half, S->ang, S->precision, S->half, S->node,
-                                       S->b_node, S->w_row, S->stream));
+    TK_CUDA(S, tk::launch_coeff_tables(S->kerr, S->variable, S->Nr, S->Nth, S->NP, S->drs,
+                                       S->dt / S->substeps, S->x_node, S->x_half, S->ang,
+                                       S->precision, S->half, S->node, S->b_node, S->w_row,
+                                       S->stream));
     S->have_coeffs = true;
     S->have_state = false;
+    S->epoch++;   // the tables' time step may have changed: recapture graphs
+    if (S->auto_k) {
+        // substeps from the stability bound at the default growth per step,
+        // then the tables again with the inner step it gives
+        double dt_max = 0.0;
+        int k = 1;
+        st = tk_stability_bound(S, kAutoGrowthPerStep, &dt_max, &k);
+        if (st != TK_OK) {
+            S->have_coeffs = false;
+            return st;
+        }
+        if (k != 1) {
+            S->substeps = k;
+            TK_CUDA(S, tk::launch_coeff_tables(S->kerr, S->variable, S->Nr, S->Nth, S->NP, S->drs,
+                                               S->dt / S->substeps, S->x_node, S->x_half, S->ang,
+                                               S->precision, S->half, S->node, S->b_node,
+                                               S->w_row, S->stream));
+        }
+    }
+    return TK_OK;
+}
+
+tk_status tk_get_substeps(const tk_solver *S, int *substeps)
+{
+    if (!S || !substeps) return fail(nullptr, TK_ERR_ARG, "tk_get_substeps: NULL argument");
+    *substeps = S->substeps;
     return TK_OK;
 }
 
@@ -270,6 +304,26 @@ tk_status tk_set_initial_data(tk_solver *S, const double *phi_re, const double *
     S->count = 0;
     S->steps_done = 0;
     return TK_OK;
+}
+
+tk_status tk_set_initial_gaussian(tk_solver *S, double amp, double center, double width,
+                                  double noise_amp, uint64_t seed)
+{
+    tk_status st = enter(S);
+    if (st != TK_OK) return st;
+    if (!S->have_coeffs)
+        return fail(S, TK_ERR_STATE, "tk_set_initial_gaussian before tk_precompute_coeffs");
+    if (!isfinite(amp) || !isfinite(center) || !(width > 0.0) || !isfinite(width) ||
+        !(noise_amp >= 0.0) || !isfinite(noise_amp))
+        return fail(S, TK_ERR_ARG, "tk_set_initial_gaussian: need finite amp and centre, width > 0, "
+                                   "noise_amp >= 0");
+    st = ensure_staging(S);
+    if (st != TK_OK) return st;
+    const size_t plane = (size_t)S->Nth * S->Nr;
+    TK_CUDA(S, tk::launch_gaussian(S->Nr, S->Nth, S->rs_min, S->drs, amp, center, width, noise_amp,
+                                   (unsigned long long)seed, S->staging, S->staging + plane,
+                                   S->stream));
+    return tk_set_initial_data(S, S->staging, S->staging + plane, nullptr, nullptr, 1);
 }
 
 tk_status tk_add_observer(tk_solver *S, double rstar_obs, double theta_obs, int *obs_id)

@@ -156,26 +156,34 @@ __device__ double sl_weight(int s, int m, double th)
 // P = sin(theta) w^2 at the faces theta = f dth (zero on both poles), Q_j the
 // mean of P over the cell by 4-point Gauss-Legendre on 64 sub-panels.
 // ang[j] = P_{j+1}/(Q_j dth^2), ang[NP + j] = P_j/(Q_j dth^2); zero on padding rows.
+// One warp per row j: lane l integrates sub-panels l and l + 32, then the
+// warp sums the 32 partial sums in a fixed tree order.
+constexpr int kStencilPanels = 64;
+
 __global__ void regular_stencil_kernel(int s, int m, int Nth, int NP, double *__restrict__ ang)
 {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.x;
+    const int lane = threadIdx.x;
     if (j >= NP) return;
     if (j >= Nth) {
-        ang[j] = 0.0;
-        ang[NP + j] = 0.0;
+        if (lane == 0) {
+            ang[j] = 0.0;
+            ang[NP + j] = 0.0;
+        }
         return;
     }
     const double dth = M_PI / Nth;
     const double xg[2] = {0.3399810435848563, 0.8611363115940526};
     const double wg[2] = {0.6521451548625461, 0.3478548451374538};
-    const int panels = 64;
-    const double h = dth / panels;
+    const double h = dth / kStencilPanels;
     double acc = 0.0;
-    for (int k = 0; k < panels; ++k) {
+    for (int k = lane; k < kStencilPanels; k += 32) {
         const double c = j * dth + (k + 0.5) * h;
         for (int g = 0; g < 2; ++g)
             acc += wg[g] * (sl_weight(s, m, c - 0.5 * h * xg[g]) + sl_weight(s, m, c + 0.5 * h * xg[g]));
     }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane != 0) return;
     const double Q = 0.5 * h * acc / dth;
     const double Plo = (j == 0) ? 0.0 : sl_weight(s, m, j * dth);
     const double Phi = (j == Nth - 1) ? 0.0 : sl_weight(s, m, (j + 1) * dth);
@@ -339,7 +347,7 @@ cudaError_t launch_coeff_tables(const Kerr &P, int variable, int Nr, int Ntheta,
                                 void *node, double *b_node, double *w_row, cudaStream_t st)
 {
     if (variable != 0) {
-        regular_stencil_kernel<<<(NP + 31) / 32, 32, 0, st>>>(P.s, P.m, Ntheta, NP, ang);
+        regular_stencil_kernel<<<NP, 32, 0, st>>>(P.s, P.m, Ntheta, NP, ang);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -18,7 +18,6 @@ constexpr int kMaxObservers = 16;
 constexpr int kMaxK = 4;          // theta rows per lane: Ntheta <= 32 * kMaxK
 constexpr int kNCH = 11;          // half-node table entries
 constexpr int kNCN = 10;          // node table entries
-constexpr int kStepThreads = 256; // threads per block of the step kernel (8 warps)
 
 // Half-node table entries (Eq. lw1 with dtau = dt/2, rho = 1/dr*):
 //   HP  = 1/2 + dtau rho b        coefficient of Phi_i   in Phi^{n+1/2}
@@ -78,6 +77,9 @@ cudaError_t launch_import_state(int precision, int Nr, int Ntheta, int NP, doubl
                                 cudaStream_t st);
 cudaError_t launch_export_state(int precision, int Nr, int Ntheta, int NP, const void *u,
                                 double *planes4, cudaStream_t st);
+cudaError_t launch_gaussian(int Nr, int Ntheta, double rs_min, double drs, double amp,
+                            double center, double width, double noise, unsigned long long seed,
+                            double *re, double *im, cudaStream_t st);
 cudaError_t launch_finite_check(int precision, size_t n, const void *u, int *flag,
                                 cudaStream_t st);
 cudaError_t launch_wave_sum(const double *wave_obs, int64_t count, double *re, double *im,
@@ -88,6 +90,7 @@ struct StepLaunch {
     int precision, K;
     int Nr, NP;
     int blocks;           // grid size (columns are split evenly over its warps)
+    int warps;            // warps per block (from step_grid_shape)
     double dt_inner;      // Lax-Wendroff step
     const void *u_in;
     void *u_out;
@@ -103,6 +106,11 @@ struct StepLaunch {
     ObsDev obs;
 };
 cudaError_t launch_lw_step(const StepLaunch &L, cudaStream_t st);
-int step_grid_blocks(int precision, int K, int Nr, int num_sms);
+// Launch shape of the step kernel for a grid: returns the number of blocks
+// and sets *warps to the warps per block.
+int step_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
+// Grid of the adjoint step kernel (blocks of four warps, one wave at most, at
+// least one column per warp).
+int adjoint_grid_blocks(int precision, int K, int Nr, int num_sms);
 
 }  // namespace tk

@@ -71,6 +71,52 @@ __global__ void wave_sum_kernel(const double *__restrict__ w, int64_t count, dou
     im[n] = w[4 * n + 1] + w[4 * n + 3];
 }
 
+// SplitMix64 (G. L. Steele, D. Lea, C. H. Flood, "Fast splittable
+// pseudorandom number generators", OOPSLA 2014) in its counter form: output k
+// (k = 0, 1, ...) of seed S is the 64-bit finaliser applied to
+// S + (k + 1) * 0x9E3779B97F4A7C15; a uniform double in [0, 1) is the top 53
+// bits times 2^-53.
+__device__ __forceinline__ double splitmix64_uniform(unsigned long long seed, unsigned long long k)
+{
+    unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * 0x1.0p-53;
+}
+
+// Gaussian pulse with the sin^2(theta) profile plus uniform noise, planes
+// [Ntheta][Nr]: re = sin^2(theta_j) * amp * exp(-(r*_i - c)^2 / (2 w^2))
+// + noise * (2 u - 1), im = noise * (2 u' - 1), with u the SplitMix64 output
+// j Nr + i and u' the output Nr Ntheta + j Nr + i.  Every operation is rounded
+// on its own (no contraction), so the planes agree with the same formula
+// evaluated one IEEE operation at a time up to the last bits of exp and sin.
+__global__ void gaussian_kernel(int Nr, int Nth, double rs_min, double drs, double dth, double amp,
+                                double center, double two_w2, double noise,
+                                unsigned long long seed, double *__restrict__ re,
+                                double *__restrict__ im)
+{
+    const long long P = (long long)Nr * Nth;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < P;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(k / Nr), i = (int)(k - (long long)j * Nr);
+        const double rs = __dadd_rn(rs_min, __dmul_rn((double)i, drs));
+        const double th = __dmul_rn(__dadd_rn((double)j, 0.5), dth);
+        const double d = __dsub_rn(rs, center);
+        const double g = __dmul_rn(amp, exp(-__ddiv_rn(__dmul_rn(d, d), two_w2)));
+        const double sn = sin(th);
+        double vr = __dmul_rn(__dmul_rn(sn, sn), g), vi = 0.0;
+        if (noise > 0.0) {
+            const double ur = splitmix64_uniform(seed, (unsigned long long)k);
+            const double ui = splitmix64_uniform(seed, (unsigned long long)(P + k));
+            vr = __dadd_rn(vr, __dmul_rn(noise, __dsub_rn(__dmul_rn(2.0, ur), 1.0)));
+            vi = __dmul_rn(noise, __dsub_rn(__dmul_rn(2.0, ui), 1.0));
+        }
+        re[k] = vr;
+        im[k] = vi;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_import_state(int precision, int Nr, int Ntheta, int NP, double drs,
@@ -116,6 +162,19 @@ cudaError_t launch_wave_sum(const double *wave_obs, int64_t count, double *re, d
     const int threads = 256;
     const int64_t blocks = (count + threads - 1) / threads;
     wave_sum_kernel<<<(unsigned)blocks, threads, 0, st>>>(wave_obs, count, re, im);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gaussian(int Nr, int Ntheta, double rs_min, double drs, double amp,
+                            double center, double width, double noise, unsigned long long seed,
+                            double *re, double *im, cudaStream_t st)
+{
+    const long long P = (long long)Nr * Ntheta;
+    long long blocks = (P + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    gaussian_kernel<<<(unsigned)blocks, 256, 0, st>>>(Nr, Ntheta, rs_min, drs, M_PI / Ntheta, amp,
+                                                      center, 2.0 * (width * width), noise, seed,
+                                                      re, im);
     return cudaGetLastError();
 }
 

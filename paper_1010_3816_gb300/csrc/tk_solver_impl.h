@@ -41,7 +41,10 @@ struct tk_solver {
     int64_t count = 0;
     int64_t steps_done = 0;
     // launch shape
-    int blocks = 1;
+    bool auto_k = false;        // substeps from the stability bound at each precompute
+    int blocks = 1;             // step kernel launch shape
+    int warps = 4;
+    int adj_blocks = 1;         // adjoint kernel grid
     // CUDA-graph replay of chunks of outer steps (0 = launch every step directly)
     int graph_chunk = -1;            // -1: choose automatically
     cudaStream_t capture_stream = nullptr;

@@ -50,30 +50,41 @@ __device__ __forceinline__ void advance_sample(const WaveArgs &wa)
     }
 }
 
-// Work split: the grid is one wave of resident blocks (SMs x blocks per SM),
-// or fewer on a small grid (at least one column per warp).  Block b owns
-// columns [b Nr / B, (b+1) Nr / B), within which its warps take contiguous
-// ranges.  Warps w and w + 4 run on the same SM sub-partition, so the four
-// quarters of the block's columns go to the four pairs and each pair splits
-// its quarter in two: every sub-partition gets the same number of columns to
-// within one, and the extra column of a pair costs no idle pipe.  A warp
-// needs the half-step value at the left edge of its range; the first warp of
-// a block recomputes it, every other warp receives it from its left
-// neighbour through shared memory once both have finished their sweep (the
-// warp's first node is deferred until then).
-// Also returns the nearest warp to the left in the block that owns columns
-// (-1 if none: this warp then recomputes its left half-step value itself).
+// Warps per block.  A "wide" launch runs one block per SM with the most warps
+// (a multiple of four) whose registers fit in the SM's register file at the
+// register count the kernel compiles to for that element type and K; a
+// "narrow" launch runs blocks of four warps, several per SM, for grids too
+// small to give every warp of a wide launch a column.
+template <typename T, int K>
+constexpr int wide_warps()
+{
+    return sizeof(T) == 8 ? (K == 1 ? 24 : K == 2 ? 16 : 8) : (K == 1 ? 32 : K == 2 ? 24 : 16);
+}
+constexpr int kNarrowWarps = 4;
+
+// Work split.  Block b owns columns [b Nr / B, (b+1) Nr / B), within which
+// its warps take contiguous ranges, in warp order.  Warps w, w + 4, w + 8,
+// ... run on the same SM sub-partition, so the four quarters of the block's
+// columns go to the four sub-partitions, and each sub-partition's warps split
+// their quarter evenly: with one block per SM every sub-partition gets the
+// same number of columns to within one.  A warp needs the half-step value at
+// the left edge of its range; the first warp of a block recomputes it, every
+// other warp receives it from its left neighbour through shared memory once
+// both have finished their sweep (the warp's first node is deferred until
+// then).  Also returns the nearest warp to the left in the block that owns
+// columns (-1 if none: this warp then recomputes its left half-step value).
+template <int W>
 __device__ __forceinline__ void warp_range(int Nr, int wib, int *i0, int *i1, int *left)
 {
-    constexpr int W = kStepThreads / 32;
+    constexpr int G = W / 4;   // warps per sub-partition
     const long long B = gridDim.x, b = blockIdx.x;
     const int b0 = (int)((b * Nr) / B), b1 = (int)(((b + 1) * Nr) / B);
     const int C = b1 - b0;
     int start = b0, cnt = 0, prev = -1;
     for (int w = 0; w <= wib; ++w) {
-        const int p = w % (W / 2);
-        const int cp = (int)(((long long)(p + 1) * C) / (W / 2) - ((long long)p * C) / (W / 2));
-        const int c = (w < W / 2) ? (cp + 1) / 2 : cp / 2;
+        const int p = w % 4, q = w / 4;
+        const int cp = ((p + 1) * C) / 4 - (p * C) / 4;
+        const int c = ((q + 1) * cp) / G - (q * cp) / G;
         if (w < wib) {
             start += c;
             if (c > 0) prev = w;
@@ -86,8 +97,8 @@ __device__ __forceinline__ void warp_range(int Nr, int wib, int *i0, int *i1, in
     *left = prev;
 }
 
-template <typename T, int K>
-__global__ void __launch_bounds__(kStepThreads)
+template <typename T, int K, int W>
+__global__ void __launch_bounds__(W * 32, wide_warps<T, K>() / W)
 lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__restrict__ half,
                const T *__restrict__ node, int Nr, T eh, T en, const WaveArgs wa)
 {
@@ -100,7 +111,7 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     int i0, i1, left;
-    warp_range(Nr, wib, &i0, &i1, &left);
+    warp_range<W>(Nr, wib, &i0, &i1, &left);
     const int row = lane * K;
     const bool lead = (left < 0);
 
@@ -172,20 +183,31 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
     if (wa.write) advance_sample(wa);
 }
 
-template <typename T, int K>
+template <typename T, int K, int W>
 constexpr size_t step_smem_bytes()
 {
-    return (size_t)(kStepThreads / 32) * 3 * 4 * 32 * K * sizeof(T);
+    return (size_t)W * 3 * 4 * 32 * K * sizeof(T);
 }
 
-// Opt the kernel in to its dynamic shared memory once (above 48 KB for K = 4).
-template <typename T, int K>
+// Opt the kernel in to its dynamic shared memory once (above 48 KB).
+template <typename T, int K, int W>
 cudaError_t step_smem_setup()
 {
-    static cudaError_t e = cudaFuncSetAttribute(lw_step_kernel<T, K>,
+    static cudaError_t e = cudaFuncSetAttribute(lw_step_kernel<T, K, W>,
                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)step_smem_bytes<T, K>());
+                                                (int)step_smem_bytes<T, K, W>());
     return e;
+}
+
+template <typename T, int K, int W>
+cudaError_t launch_shape(const StepLaunch &L, const WaveArgs &wa, cudaStream_t st)
+{
+    cudaError_t e = step_smem_setup<T, K, W>();
+    if (e != cudaSuccess) return e;
+    lw_step_kernel<T, K, W><<<L.blocks, W * 32, step_smem_bytes<T, K, W>(), st>>>(
+        (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node, L.Nr,
+        (T)(0.25 * L.dt_inner), (T)(0.5 * L.dt_inner), wa);
+    return cudaGetLastError();
 }
 
 template <typename T, int K>
@@ -199,44 +221,53 @@ cudaError_t launch_typed(const StepLaunch &L, cudaStream_t st)
     wa.wave = L.wave;
     wa.w_row = L.w_row;
     wa.obs = L.obs;
-    cudaError_t e = step_smem_setup<T, K>();
-    if (e != cudaSuccess) return e;
-    lw_step_kernel<T, K><<<L.blocks, kStepThreads, step_smem_bytes<T, K>(), st>>>(
-        (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node, L.Nr,
-        (T)(0.25 * L.dt_inner), (T)(0.5 * L.dt_inner), wa);
-    return cudaGetLastError();
+    if (L.warps == wide_warps<T, K>()) return launch_shape<T, K, wide_warps<T, K>()>(L, wa, st);
+    if (L.warps == kNarrowWarps) return launch_shape<T, K, kNarrowWarps>(L, wa, st);
+    return cudaErrorInvalidValue;
 }
 
-template <typename T, int K>
+template <typename T, int K, int W>
 int resident_blocks()
 {
     int n = 0;
-    if (step_smem_setup<T, K>() != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_step_kernel<T, K>, kStepThreads,
-                                                      step_smem_bytes<T, K>()) != cudaSuccess)
-        n = 1;
-    return n < 1 ? 1 : n;
+    if (step_smem_setup<T, K, W>() != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_step_kernel<T, K, W>, W * 32,
+                                                      step_smem_bytes<T, K, W>()) != cudaSuccess)
+        n = 0;
+    return n;
+}
+
+template <typename T, int K>
+int grid_shape(int Nr, int num_sms, int *warps)
+{
+    // Wide when every warp of one block per SM gets a column and the block
+    // fits; otherwise narrow blocks, one wave of them at most and at least
+    // one column per warp (on a small grid every warp's sweep is
+    // latency-bound, and shorter sweeps finish sooner).
+    constexpr int WW = wide_warps<T, K>();
+    if ((long long)Nr >= (long long)num_sms * WW && resident_blocks<T, K, WW>() >= 1) {
+        *warps = WW;
+        return num_sms;
+    }
+    *warps = kNarrowWarps;
+    int per_sm = resident_blocks<T, K, kNarrowWarps>();
+    if (per_sm < 1) per_sm = 1;
+    int blocks = num_sms * per_sm;
+    if (blocks > Nr / kNarrowWarps) blocks = Nr / kNarrowWarps;
+    return blocks < 1 ? 1 : blocks;
 }
 
 }  // namespace
 
-int step_grid_blocks(int precision, int K, int Nr, int num_sms)
+int step_grid_shape(int precision, int K, int Nr, int num_sms, int *warps)
 {
-    int per_sm = 1;
     if (precision == 0)
-        per_sm = K == 1 ? resident_blocks<double, 1>() : K == 2 ? resident_blocks<double, 2>()
-                                                                : resident_blocks<double, 4>();
-    else
-        per_sm = K == 1 ? resident_blocks<float, 1>() : K == 2 ? resident_blocks<float, 2>()
-                                                               : resident_blocks<float, 4>();
-    // One wave of resident blocks (a multiple of the SM count) when the grid
-    // is large; for a small grid, as many warps as columns, since there every
-    // warp's sweep is latency-bound and shorter sweeps finish sooner.
-    const int W = kStepThreads / 32;
-    int blocks = num_sms * per_sm;
-    const int max_blocks = Nr / W;   // every warp keeps at least one column
-    if (blocks > max_blocks) blocks = max_blocks;
-    return blocks < 1 ? 1 : blocks;
+        return K == 1 ? grid_shape<double, 1>(Nr, num_sms, warps)
+             : K == 2 ? grid_shape<double, 2>(Nr, num_sms, warps)
+                      : grid_shape<double, 4>(Nr, num_sms, warps);
+    return K == 1 ? grid_shape<float, 1>(Nr, num_sms, warps)
+         : K == 2 ? grid_shape<float, 2>(Nr, num_sms, warps)
+                  : grid_shape<float, 4>(Nr, num_sms, warps);
 }
 
 cudaError_t launch_lw_step(const StepLaunch &L, cudaStream_t st)
