@@ -54,6 +54,30 @@ FP64_FMA_PER_CLK_PER_SM = 2        # measured: 1.19 TFLOP/s at 1995 MHz on 152 S
 FP32_FMA_PER_CLK_PER_SM = 128
 
 
+# DRAM bytes per launch of the step kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture of the current kernel source),
+# keyed by (workload, precision); the capture's command and figures are in the
+# named summary under profiles/.
+MEASURED_TRAFFIC = {
+    ("kerr", 0): (333.902592e6 + 38.241280e6, "profiles/lw_step_f64_kerr_25601x64.md"),
+}
+L2_FLUSH_BYTES = 256 << 20          # twice the 129 MB L2
+
+
+class L2Flush:
+    """Writes a buffer twice the size of L2 on the stream, evicting every line
+    the previous step left behind."""
+
+    def __init__(self, torch):
+        self.buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def __call__(self):
+        self.buf.zero_()
+
+
+L2_NOTE = "L2 flushed (256 MB write) before every timed step, inside the timed region"
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -190,7 +214,7 @@ def _config(w, args, world):
             "precision": "f32" if args.precision else "f64",
             "observers": [list(o) for o in w.observers],
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "l2": "inputs larger than L2 (state 2x{:.0f} MB + tables {:.0f} MB)".format(
+            "l2": L2_NOTE + "; working set: state 2x{:.1f} MB + tables {:.1f} MB".format(
                 w.points * STATE_BYTES_PER_UPDATE[args.precision] / 1e6,
                 w.points * TABLE_BYTES_PER_UPDATE[args.precision] / 1e6)}
 
@@ -250,7 +274,9 @@ def run_batched(args, tk, torch, rank, world, local):
             for k, a, b in o:
                 tk.tk_extract(g.h, k, a, b)
 
+    flush = L2Flush(torch)
     for _ in range(args.warmup):
+        flush()
         solve(False)
     torch.cuda.synchronize()
     D.barrier()
@@ -260,6 +286,7 @@ def run_batched(args, tk, torch, rank, world, local):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
+        flush()
         solve(True)
     t1.record(stream)
     torch.cuda.synchronize()
@@ -295,7 +322,7 @@ def run_batched(args, tk, torch, rank, world, local):
                        "segment_autotuned": seg, "tuned_ms_per_outer_step": tuned_ms,
                        "grid_blocks": info["blocks"],
                        "parallelism": f"instances sharded over {world} GPUs" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2"},
+                       "l2": L2_NOTE},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": None, "kernel": "batch_step_kernel<double>",
                          "peak_source": "152 SMs x 2 DFMA/clk (measured) x 2 flop x median SM clock"},
@@ -315,7 +342,9 @@ def run_adjoint(args, tk, torch, rank, world, local):
     respect to the amplitude, centre and width of the initial pulse: forward
     solve, then the adjoint sweep (tk_adjoint) through torch.autograd."""
     w = ADJOINT_16001x128
-    n_outer = args.outer_steps or 2000
+    # t = 400 M by default: the pulse launched at r* = 50 has passed the observer
+    # at r* = 400, so the misfit and its gradient are not zero
+    n_outer = args.outer_steps or 12800
     stream = torch.cuda.current_stream()
     g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
                   substeps=w.substeps, variable=w.variable, stream=stream.cuda_stream)
@@ -355,7 +384,9 @@ def run_adjoint(args, tk, torch, rank, world, local):
             ev_b.append((e[1], e[2]))
         return [x.grad for x in p]
 
+    flush = L2Flush(torch)
     for _ in range(args.warmup):
+        flush()
         gradient(False)
     torch.cuda.synchronize()
     clocks = ClockSampler(_gpu_id(torch, local))
@@ -364,6 +395,7 @@ def run_adjoint(args, tk, torch, rank, world, local):
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
+        flush()
         grads = gradient(True)
     t1.record(stream)
     torch.cuda.synchronize()
@@ -383,7 +415,7 @@ def run_adjoint(args, tk, torch, rank, world, local):
                        "outer_steps": n_outer, "outer_steps_of_full_run": w.steps,
                        "substeps": w.substeps, "loss": "sum_t |W(t) - W_target(t)|^2 at (400, pi/2)",
                        "gradient_wrt": ["amplitude", "centre", "width", "initial planes"],
-                       "parallelism": "single GPU", "l2": "inputs larger than L2"},
+                       "parallelism": "single GPU", "l2": L2_NOTE},
             "forward_updates_per_s": inner / fwd, "adjoint_updates_per_s": inner / bwd,
             "grad": [float(x) for x in grads],
             "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
@@ -462,7 +494,9 @@ def main() -> int:
         for k, (a, b) in zip(obs_ids, obs_out):
             tk.tk_extract(solver.h, k, a, b)
 
+    flush = L2Flush(torch)
     for _ in range(args.warmup):
+        flush()
         solve_device(False)
     torch.cuda.synchronize()
     if dist:
@@ -474,6 +508,7 @@ def main() -> int:
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
     for _ in range(args.steps):
+        flush()
         solve_device(True)
     t_end.record(stream)
     torch.cuda.synchronize()
@@ -491,23 +526,24 @@ def main() -> int:
     kern_s = statistics.mean(step_ms) * 1e-3 / (n_outer * w.substeps)   # per launch
     pts = w.points
     f_clk = (clk.get("sm_mhz") or 2070.0) * 1e6
+    traffic, traffic_src = MEASURED_TRAFFIC.get((args.workload, args.precision), (None, None))
     if args.precision == 0:
         achieved = FP64_FLOP_PER_UPDATE * pts / kern_s / 1e12
         peak = NUM_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * f_clk / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "lw_step_kernel<double>",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "lw_step_kernel<double>",
                 "peak_source": "152 SMs x 2 DFMA/clk (measured) x 2 flop x median SM clock "
                                f"{f_clk / 1e6:.0f} MHz",
-                "flop_per_update": FP64_FLOP_PER_UPDATE,
+                "traffic_source": traffic_src, "flop_per_update": FP64_FLOP_PER_UPDATE,
                 "fp64_issue_frac": FP64_INSTR_PER_UPDATE * pts / kern_s /
                 (NUM_SMS * FP64_FMA_PER_CLK_PER_SM * f_clk),
                 "launch_us": kern_s * 1e6}
     else:
         achieved = STATE_BYTES_PER_UPDATE[1] * pts / kern_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": 6794.1, "unit": "GB/s",
-                "frac": achieved / 6794.1, "traffic": None, "kernel": "lw_step_kernel<float>",
+                "frac": achieved / 6794.1, "traffic": traffic, "kernel": "lw_step_kernel<float>",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                "launch_us": kern_s * 1e6}
+                "traffic_source": traffic_src, "launch_us": kern_s * 1e6}
     sb = STATE_BYTES_PER_UPDATE[args.precision] * pts / kern_s / 1e9
     tb = TABLE_BYTES_PER_UPDATE[args.precision] * pts / kern_s / 1e9
     roof_hbm = {"bound": "hbm", "achieved": sb, "peak": 6794.1, "unit": "GB/s",
@@ -537,6 +573,7 @@ def main() -> int:
             dist.barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
+            flush()
             solve_host()
         torch.cuda.synchronize()
         es = time.perf_counter() - t0

@@ -16,14 +16,13 @@
 // gradient enters as a source on the adjoint state of that step.
 //
 // A warp owns all theta rows of a range of output columns and walks it left
-// to right, recomputing eta at the left edge of its range.
+// to right; the work split and the hand-off of the left-edge eta between the
+// warps of a block are those of the forward step kernel.
 #include "tk_solver_impl.h"
 #include "tk_stencil.cuh"
 
 namespace tk {
 namespace {
-
-constexpr int kAdjThreads = 128;
 
 struct InjectArgs {
     int on;                  // add the observation gradient of sample `sample`
@@ -65,34 +64,32 @@ __device__ __forceinline__ void load_lam(const T *__restrict__ lam, int i, int N
     if (i == 0 || i == Nr - 1) zero_col<T, K>(l);
 }
 
-// Theta-neighbour part of a transposed coupling: for z+ = KP * x (sent to
-// row j+1) and z- = KM * x (sent to row j-1), the amount row j receives.
+// Transposed theta coupling: with the forward coupling sending KP_j x_j to
+// row j+1 and KM_j x_j to row j-1, row j receives
+//   KP_{j-1} x_{j-1} + KM_{j+1} x_{j+1}
+// for both components xr, xi.  The coefficients and the values are shuffled
+// separately, which costs two FP64 operations per component.  Row 0 has no
+// row -1 and the last padded row no row below: the shuffles return the lane's
+// own values there, so those coefficients are masked to zero.
 template <typename T, int K>
-__device__ __forceinline__ void neighbour_in(const T (&kp)[K], const T (&km)[K], const T (&x)[K],
-                                             T (&out)[K])
+__device__ __forceinline__ void neighbour_in(const T (&kp)[K], const T (&km)[K], const T (&xr)[K],
+                                             const T (&xi)[K], T (&outr)[K], T (&outi)[K])
 {
-    T zp[K], zm[K], dn[K], up[K];
-#pragma unroll
-    for (int t = 0; t < K; ++t) {
-        zp[t] = kp[t] * x[t];
-        zm[t] = km[t] * x[t];
-    }
-    // row j receives zp from row j-1 (the "dn" neighbour) and zm from row j+1 ("up")
-    T tmp_up[K], tmp_dn[K];
-    theta_neighbours<T, K>(zp, tmp_up, dn);
-    theta_neighbours<T, K>(zm, up, tmp_dn);
     const int lane = threadIdx.x & 31;
+    const T kp_prv = __shfl_up_sync(kFull, kp[K - 1], 1);
+    const T km_nxt = __shfl_down_sync(kFull, km[0], 1);
+    T xru[K], xrd[K], xiu[K], xid[K];
+    theta_neighbours<T, K>(xr, xru, xrd);
+    theta_neighbours<T, K>(xi, xiu, xid);
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-        // lane 0's row 0 has no row -1 and lane 31's last row no row N: the
-        // shuffles return the lane's own values there, whose coefficients are 0
-        // only on the sending side, so mask them explicitly
-        const T a = (lane == 0 && t == 0) ? T(0) : dn[t];
-        const T b = (lane == 31 && t == K - 1) ? T(0) : up[t];
-        out[t] = a + b;
+        T kpd = (t > 0) ? kp[t - 1] : kp_prv;
+        T kmu = (t + 1 < K) ? km[t + 1] : km_nxt;
+        if (t == 0 && lane == 0) kpd = T(0);
+        if (t == K - 1 && lane == 31) kmu = T(0);
+        outr[t] = fma(kpd, xrd[t], kmu * xru[t]);
+        outi[t] = fma(kpd, xid[t], kmu * xiu[t]);
     }
-    (void)tmp_up;
-    (void)tmp_dn;
 }
 
 // Node n's theta-neighbour sources Z_n = (KP_n lamPi_n)(j-1) + (KM_n lamPi_n)(j+1).
@@ -104,8 +101,7 @@ __device__ __forceinline__ void node_z(const T *__restrict__ ntab, const T (&l)[
     T kp[K], km[K];
     ldk<T, K>(ntab + N_KP * NP, kp);
     ldk<T, K>(ntab + N_KM * NP, km);
-    neighbour_in<T, K>(kp, km, l[2], zr);
-    neighbour_in<T, K>(kp, km, l[3], zi);
+    neighbour_in<T, K>(kp, km, l[2], l[3], zr, zi);
 }
 
 // eta at the half node between nodes a (left) and c (right).
@@ -154,8 +150,7 @@ __device__ __forceinline__ void half_y(const T *__restrict__ htab, const T (&h)[
     T kp[K], km[K];
     ldk<T, K>(htab + H_KP * NP, kp);
     ldk<T, K>(htab + H_KM * NP, km);
-    neighbour_in<T, K>(kp, km, h[2], yr);
-    neighbour_in<T, K>(kp, km, h[3], yi);
+    neighbour_in<T, K>(kp, km, h[2], h[3], yr, yi);
 }
 
 // mu at node i from lam~_i, eta+ (half node i+1/2: u_i is its "a") and eta-
@@ -197,68 +192,128 @@ __device__ __forceinline__ void mu_node(const T (&l)[4][K], const T (&ep)[4][K],
     }
 }
 
+// Warps per block of the wide launch (one block per SM): the most warps, in
+// multiples of four, whose registers fit in the register file at the count
+// the kernel compiles to for this element type and K.
 template <typename T, int K>
-__global__ void __launch_bounds__(kAdjThreads)
+constexpr int adj_wide_warps()
+{
+    return sizeof(T) == 8 ? (K == 1 ? 24 : K == 2 ? 16 : 8) : (K == 1 ? 32 : K == 2 ? 24 : 12);
+}
+
+// Shared memory per warp, in theta-columns of NP values: [0, 6) eta at the
+// warp's last half node with its neighbour sources (read by the right
+// neighbour), [6, 16) lam~, eta+ and its sources at the warp's first column
+// (its deferred node).
+constexpr int kAdjShared = 16;
+
+template <typename T, int K, int W>
+__global__ void __launch_bounds__(W * 32, adj_wide_warps<T, K>() / W)
 lw_adjoint_kernel(const T *__restrict__ lam, T *__restrict__ mu_out, const T *__restrict__ half,
                   const T *__restrict__ node, int Nr, T eh, T en, const InjectArgs inj)
 {
     constexpr int NP = 32 * K;
     constexpr size_t SP = 4 * NP, HP = (size_t)kNCH * NP, NQ = (size_t)kNCN * NP;
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    T(*sh)[kAdjShared][NP] = reinterpret_cast<T(*)[kAdjShared][NP]>(sh_raw);
     const int lane = threadIdx.x & 31;
-    const long long G = (long long)gridDim.x * (kAdjThreads / 32);
-    const long long g = (long long)blockIdx.x * (kAdjThreads / 32) + (threadIdx.x >> 5);
-    const int i0 = (int)((g * Nr) / G);
-    const int i1 = (int)(((g + 1) * Nr) / G);
-    if (i1 <= i0) return;
+    const int wib = threadIdx.x >> 5;
+    int i0, i1, left;
+    warp_range<W>(Nr, wib, &i0, &i1, &left);
     const int row = lane * K;
+    const bool lead = (left < 0);
 
     T la[4][K], zar[K], zai[K];        // node i: lam~ and its neighbour sources
     T em[4][K], ymr[K], ymi[K];        // half node i-1/2: eta and its neighbour sources
-    load_lam<T, K>(lam, i0, Nr, lane, inj, la);
-    node_z<T, K>(node + (size_t)i0 * NQ + row, la, zar, zai);
-    if (i0 > 0) {
-        T ll[4][K], zlr[K], zli[K];
-        load_lam<T, K>(lam, i0 - 1, Nr, lane, inj, ll);
-        node_z<T, K>(node + (size_t)(i0 - 1) * NQ + row, ll, zlr, zli);
-        eta_half<T, K>(ll, la, zlr, zli, zar, zai, node + (size_t)(i0 - 1) * NQ + row,
-                       node + (size_t)i0 * NQ + row, en, em);
-        half_y<T, K>(half + (size_t)(i0 - 1) * HP + row, em, ymr, ymi);
-    } else {
-        zero_col<T, K>(em);
+    zero_col<T, K>(em);
 #pragma unroll
-        for (int t = 0; t < K; ++t) ymr[t] = ymi[t] = T(0);
-    }
-    for (int i = i0; i < i1; ++i) {
-        T lc[4][K], zcr[K], zci[K], ep[4][K], ypr[K], ypi[K], mu[4][K];
-        if (i + 1 < Nr) {
-            load_lam<T, K>(lam, i + 1, Nr, lane, inj, lc);
-            node_z<T, K>(node + (size_t)(i + 1) * NQ + row, lc, zcr, zci);
-            eta_half<T, K>(la, lc, zar, zai, zcr, zci, node + (size_t)i * NQ + row,
-                           node + (size_t)(i + 1) * NQ + row, en, ep);
-            half_y<T, K>(half + (size_t)i * HP + row, ep, ypr, ypi);
-        } else {
-            zero_col<T, K>(lc);
-            zero_col<T, K>(ep);
-#pragma unroll
-            for (int t = 0; t < K; ++t) zcr[t] = zci[t] = ypr[t] = ypi[t] = T(0);
+    for (int t = 0; t < K; ++t) ymr[t] = ymi[t] = T(0);
+    if (i1 > i0) {
+        load_lam<T, K>(lam, i0, Nr, lane, inj, la);
+        node_z<T, K>(node + (size_t)i0 * NQ + row, la, zar, zai);
+        if (lead && i0 > 0) {
+            T ll[4][K], zlr[K], zli[K];
+            load_lam<T, K>(lam, i0 - 1, Nr, lane, inj, ll);
+            node_z<T, K>(node + (size_t)(i0 - 1) * NQ + row, ll, zlr, zli);
+            eta_half<T, K>(ll, la, zlr, zli, zar, zai, node + (size_t)(i0 - 1) * NQ + row,
+                           node + (size_t)i0 * NQ + row, en, em);
+            half_y<T, K>(half + (size_t)(i0 - 1) * HP + row, em, ymr, ymi);
         }
-        const T *hm_tab = half + (size_t)(i > 0 ? i - 1 : 0) * HP + row;
-        mu_node<T, K>(la, ep, em, ypr, ypi, ymr, ymi, half + (size_t)i * HP + row, hm_tab, eh, mu);
-        store_col<T, K>(mu_out + (size_t)i * SP + row, mu);
+        for (int i = i0; i < i1; ++i) {
+            T lc[4][K], zcr[K], zci[K], ep[4][K], ypr[K], ypi[K];
+            if (i + 1 < Nr) {
+                load_lam<T, K>(lam, i + 1, Nr, lane, inj, lc);
+                node_z<T, K>(node + (size_t)(i + 1) * NQ + row, lc, zcr, zci);
+                eta_half<T, K>(la, lc, zar, zai, zcr, zci, node + (size_t)i * NQ + row,
+                               node + (size_t)(i + 1) * NQ + row, en, ep);
+                half_y<T, K>(half + (size_t)i * HP + row, ep, ypr, ypi);
+            } else {
+                zero_col<T, K>(lc);
+                zero_col<T, K>(ep);
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
+                for (int t = 0; t < K; ++t) zcr[t] = zci[t] = ypr[t] = ypi[t] = T(0);
+            }
+            if (i == i0 && !lead) {
 #pragma unroll
-            for (int t = 0; t < K; ++t) {
-                la[c][t] = lc[c][t];
-                em[c][t] = ep[c][t];
+                for (int t = 0; t < K; ++t) {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        sh[wib][6 + c][row + t] = la[c][t];
+                        sh[wib][10 + c][row + t] = ep[c][t];
+                    }
+                    sh[wib][14][row + t] = ypr[t];
+                    sh[wib][15][row + t] = ypi[t];
+                }
+            } else {
+                T mu[4][K];
+                const T *hm_tab = half + (size_t)(i > 0 ? i - 1 : 0) * HP + row;
+                mu_node<T, K>(la, ep, em, ypr, ypi, ymr, ymi, half + (size_t)i * HP + row, hm_tab,
+                              eh, mu);
+                store_col<T, K>(mu_out + (size_t)i * SP + row, mu);
             }
 #pragma unroll
-        for (int t = 0; t < K; ++t) {
-            zar[t] = zcr[t];
-            zai[t] = zci[t];
-            ymr[t] = ypr[t];
-            ymi[t] = ypi[t];
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    la[c][t] = lc[c][t];
+                    em[c][t] = ep[c][t];
+                }
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+                zar[t] = zcr[t];
+                zai[t] = zci[t];
+                ymr[t] = ypr[t];
+                ymi[t] = ypi[t];
+            }
         }
+    }
+    // em, ymr, ymi now belong to the half node i1 - 1/2: the right neighbour's left edge
+#pragma unroll
+    for (int t = 0; t < K; ++t) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) sh[wib][c][row + t] = em[c][t];
+        sh[wib][4][row + t] = ymr[t];
+        sh[wib][5][row + t] = ymi[t];
+    }
+    __syncthreads();
+    if (!lead && i1 > i0) {
+        T l0[4][K], ep[4][K], el[4][K], ypr[K], ypi[K], yml[K], ymli[K], mu[4][K];
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                el[c][t] = sh[left][c][row + t];
+                l0[c][t] = sh[wib][6 + c][row + t];
+                ep[c][t] = sh[wib][10 + c][row + t];
+            }
+            yml[t] = sh[left][4][row + t];
+            ymli[t] = sh[left][5][row + t];
+            ypr[t] = sh[wib][14][row + t];
+            ypi[t] = sh[wib][15][row + t];
+        }
+        mu_node<T, K>(l0, ep, el, ypr, ypi, yml, ymli, half + (size_t)i0 * HP + row,
+                      half + (size_t)(i0 - 1) * HP + row, eh, mu);
+        store_col<T, K>(mu_out + (size_t)i0 * SP + row, mu);
     }
 }
 
@@ -290,55 +345,98 @@ __global__ void initial_transpose_kernel(int Nr, int Nth, int NP, double drs,
     for (int c = 0; c < nout; ++c) out[c * plane + k] = g[c];
 }
 
-template <typename T, int K>
-cudaError_t launch_adj(const void *lam, void *mu, const void *half, const void *node, int Nr,
-                       int blocks, double dt_in, const InjectArgs &inj, cudaStream_t st)
+template <typename T, int K, int W>
+constexpr size_t adj_smem_bytes()
 {
-    lw_adjoint_kernel<T, K><<<blocks, kAdjThreads, 0, st>>>((const T *)lam, (T *)mu, (const T *)half,
-                                                            (const T *)node, Nr, (T)(0.25 * dt_in),
-                                                            (T)(0.5 * dt_in), inj);
+    return (size_t)W * kAdjShared * 32 * K * sizeof(T);
+}
+
+template <typename T, int K, int W>
+cudaError_t adj_smem_setup()
+{
+    static cudaError_t e = cudaFuncSetAttribute(lw_adjoint_kernel<T, K, W>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)adj_smem_bytes<T, K, W>());
+    return e;
+}
+
+template <typename T, int K, int W>
+cudaError_t launch_adj_shape(const void *lam, void *mu, const void *half, const void *node,
+                             int Nr, int blocks, double dt_in, const InjectArgs &inj,
+                             cudaStream_t st)
+{
+    cudaError_t e = adj_smem_setup<T, K, W>();
+    if (e != cudaSuccess) return e;
+    lw_adjoint_kernel<T, K, W><<<blocks, W * 32, adj_smem_bytes<T, K, W>(), st>>>(
+        (const T *)lam, (T *)mu, (const T *)half, (const T *)node, Nr, (T)(0.25 * dt_in),
+        (T)(0.5 * dt_in), inj);
     return cudaGetLastError();
 }
 
+template <typename T, int K>
+cudaError_t launch_adj(const void *lam, void *mu, const void *half, const void *node, int Nr,
+                       int blocks, int warps, double dt_in, const InjectArgs &inj, cudaStream_t st)
+{
+    constexpr int WW = adj_wide_warps<T, K>();
+    if (warps == WW)
+        return launch_adj_shape<T, K, WW>(lam, mu, half, node, Nr, blocks, dt_in, inj, st);
+    if (warps == kNarrowWarps)
+        return launch_adj_shape<T, K, kNarrowWarps>(lam, mu, half, node, Nr, blocks, dt_in, inj, st);
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_adjoint_step(int precision, int K, const void *lam, void *mu, const void *half,
-                                const void *node, int Nr, int blocks, double dt_in,
+                                const void *node, int Nr, int blocks, int warps, double dt_in,
                                 const InjectArgs &inj, cudaStream_t st)
 {
     if (precision == 0) {
-        if (K == 1) return launch_adj<double, 1>(lam, mu, half, node, Nr, blocks, dt_in, inj, st);
-        if (K == 2) return launch_adj<double, 2>(lam, mu, half, node, Nr, blocks, dt_in, inj, st);
-        return launch_adj<double, 4>(lam, mu, half, node, Nr, blocks, dt_in, inj, st);
+        if (K == 1) return launch_adj<double, 1>(lam, mu, half, node, Nr, blocks, warps, dt_in, inj, st);
+        if (K == 2) return launch_adj<double, 2>(lam, mu, half, node, Nr, blocks, warps, dt_in, inj, st);
+        return launch_adj<double, 4>(lam, mu, half, node, Nr, blocks, warps, dt_in, inj, st);
     }
-    if (K == 1) return launch_adj<float, 1>(lam, mu, half, node, Nr, blocks, dt_in, inj, st);
-    if (K == 2) return launch_adj<float, 2>(lam, mu, half, node, Nr, blocks, dt_in, inj, st);
-    return launch_adj<float, 4>(lam, mu, half, node, Nr, blocks, dt_in, inj, st);
+    if (K == 1) return launch_adj<float, 1>(lam, mu, half, node, Nr, blocks, warps, dt_in, inj, st);
+    if (K == 2) return launch_adj<float, 2>(lam, mu, half, node, Nr, blocks, warps, dt_in, inj, st);
+    return launch_adj<float, 4>(lam, mu, half, node, Nr, blocks, warps, dt_in, inj, st);
 }
 
-template <typename T, int K>
+template <typename T, int K, int W>
 int adj_resident()
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_adjoint_kernel<T, K>, kAdjThreads, 0) !=
-        cudaSuccess)
-        n = 1;
-    return n < 1 ? 1 : n;
+    if (adj_smem_setup<T, K, W>() != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_adjoint_kernel<T, K, W>, W * 32,
+                                                      adj_smem_bytes<T, K, W>()) != cudaSuccess)
+        n = 0;
+    return n;
+}
+
+template <typename T, int K>
+int adj_shape(int Nr, int num_sms, int *warps)
+{
+    constexpr int WW = adj_wide_warps<T, K>();
+    if ((long long)Nr >= (long long)num_sms * WW && adj_resident<T, K, WW>() >= 1) {
+        *warps = WW;
+        return num_sms;
+    }
+    *warps = kNarrowWarps;
+    int per_sm = adj_resident<T, K, kNarrowWarps>();
+    if (per_sm < 1) per_sm = 1;
+    int blocks = num_sms * per_sm;
+    if (blocks > Nr / kNarrowWarps) blocks = Nr / kNarrowWarps;
+    return blocks < 1 ? 1 : blocks;
 }
 
 }  // namespace
 
-int adjoint_grid_blocks(int precision, int K, int Nr, int num_sms)
+int adjoint_grid_shape(int precision, int K, int Nr, int num_sms, int *warps)
 {
-    int per_sm;
     if (precision == 0)
-        per_sm = K == 1 ? adj_resident<double, 1>() : K == 2 ? adj_resident<double, 2>()
-                                                             : adj_resident<double, 4>();
-    else
-        per_sm = K == 1 ? adj_resident<float, 1>() : K == 2 ? adj_resident<float, 2>()
-                                                            : adj_resident<float, 4>();
-    int blocks = num_sms * per_sm;
-    const int max_blocks = Nr / (kAdjThreads / 32);
-    if (blocks > max_blocks) blocks = max_blocks;
-    return blocks < 1 ? 1 : blocks;
+        return K == 1 ? adj_shape<double, 1>(Nr, num_sms, warps)
+             : K == 2 ? adj_shape<double, 2>(Nr, num_sms, warps)
+                      : adj_shape<double, 4>(Nr, num_sms, warps);
+    return K == 1 ? adj_shape<float, 1>(Nr, num_sms, warps)
+         : K == 2 ? adj_shape<float, 2>(Nr, num_sms, warps)
+                  : adj_shape<float, 4>(Nr, num_sms, warps);
 }
 
 }  // namespace tk
@@ -420,7 +518,7 @@ extern "C" tk_status tk_adjoint(tk_solver *S, const double *dL_dwave, const doub
             inj.on = (k == 0) && dwave != nullptr;
             inj.sample = t;
             e = tk::launch_adjoint_step(S->precision, S->K, S->adj[cur], S->adj[cur ^ 1], S->half,
-                                        S->node, S->Nr, S->adj_blocks, dt_in, inj, S->stream);
+                                        S->node, S->Nr, S->adj_blocks, S->adj_warps, dt_in, inj, S->stream);
             cur ^= 1;
         }
     if (e != cudaSuccess) {

@@ -178,7 +178,7 @@ tk_status tk_make_grid(tk_solver **out, double rstar_min, double rstar_max, int 
     S->drs = (rstar_max - rstar_min) / (Nr - 1);
     S->dt = dt;
     S->blocks = tk::step_grid_shape(precision, S->K, Nr, S->num_sms, &S->warps);
-    S->adj_blocks = tk::adjoint_grid_blocks(precision, S->K, Nr, S->num_sms);
+    S->adj_blocks = tk::adjoint_grid_shape(precision, S->K, Nr, S->num_sms, &S->adj_warps);
 
     const size_t se = state_elems(S);
     tk_status st = TK_OK;

@@ -109,8 +109,8 @@ cudaError_t launch_lw_step(const StepLaunch &L, cudaStream_t st);
 // Launch shape of the step kernel for a grid: returns the number of blocks
 // and sets *warps to the warps per block.
 int step_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
-// Grid of the adjoint step kernel (blocks of four warps, one wave at most, at
-// least one column per warp).
-int adjoint_grid_blocks(int precision, int K, int Nr, int num_sms);
+// Launch shape of the adjoint step kernel: returns the number of blocks and
+// sets *warps to the warps per block.
+int adjoint_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
 
 }  // namespace tk

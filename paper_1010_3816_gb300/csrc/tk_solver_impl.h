@@ -44,7 +44,8 @@ struct tk_solver {
     bool auto_k = false;        // substeps from the stability bound at each precompute
     int blocks = 1;             // step kernel launch shape
     int warps = 4;
-    int adj_blocks = 1;         // adjoint kernel grid
+    int adj_blocks = 1;         // adjoint kernel launch shape
+    int adj_warps = 4;
     // CUDA-graph replay of chunks of outer steps (0 = launch every step directly)
     int graph_chunk = -1;            // -1: choose automatically
     cudaStream_t capture_stream = nullptr;

@@ -95,6 +95,43 @@ __device__ __forceinline__ void theta_neighbours(const T (&s)[K], T (&up)[K], T 
     }
 }
 
+constexpr int kNarrowWarps = 4;   // warps per block of a narrow launch
+
+// Work split.  Block b owns columns [b Nr / B, (b+1) Nr / B), within which
+// its warps take contiguous ranges, in warp order.  Warps w, w + 4, w + 8,
+// ... run on the same SM sub-partition, so the four quarters of the block's
+// columns go to the four sub-partitions, and each sub-partition's warps split
+// their quarter evenly: with one block per SM every sub-partition gets the
+// same number of columns to within one.  A warp needs the half-step value at
+// the left edge of its range; the first warp of a block recomputes it, every
+// other warp receives it from its left neighbour through shared memory once
+// both have finished their sweep (the warp's first node is deferred until
+// then).  Also returns the nearest warp to the left in the block that owns
+// columns (-1 if none: this warp then recomputes its left half-step value).
+template <int W>
+__device__ __forceinline__ void warp_range(int Nr, int wib, int *i0, int *i1, int *left)
+{
+    constexpr int G = W / 4;   // warps per sub-partition
+    const long long B = gridDim.x, b = blockIdx.x;
+    const int b0 = (int)((b * Nr) / B), b1 = (int)(((b + 1) * Nr) / B);
+    const int C = b1 - b0;
+    int start = b0, cnt = 0, prev = -1;
+    for (int w = 0; w <= wib; ++w) {
+        const int p = w % 4, q = w / 4;
+        const int cp = ((p + 1) * C) / 4 - (p * C) / 4;
+        const int c = ((q + 1) * cp) / G - (q * cp) / G;
+        if (w < wib) {
+            start += c;
+            if (c > 0) prev = w;
+        } else {
+            cnt = c;
+        }
+    }
+    *i0 = start;
+    *i1 = start + cnt;
+    *left = prev;
+}
+
 // Eq. (lw1): u^{n+1/2}_{i+1/2} from a = u^n_i and c = u^n_{i+1}.
 template <typename T, int K>
 __device__ __forceinline__ void half_node(const T (&a)[4][K], const T (&c)[4][K],
