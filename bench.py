@@ -56,10 +56,11 @@ FP32_FMA_PER_CLK_PER_SM = 128
 
 # DRAM bytes per launch of the step kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the current kernel source),
-# keyed by (workload, precision); the capture's command and figures are in the
+# keyed by (workload name, precision); the capture's command and figures are in the
 # named summary under profiles/.
 MEASURED_TRAFFIC = {
-    ("kerr", 0): (333.902592e6 + 38.241280e6, "profiles/lw_step_f64_kerr_25601x64.md"),
+    ("kerr_a0.9_25601x64_38400steps", 0): (333.902592e6 + 38.241280e6,
+                                           "profiles/lw_step_f64_kerr_25601x64.md"),
 }
 L2_FLUSH_BYTES = 256 << 20          # twice the 129 MB L2
 
@@ -204,6 +205,17 @@ def run_reference(args, w):
     }
     print(json.dumps(line))
     return 0
+
+
+def _variant_name(w, base) -> str:
+    parts = [base.name]
+    if w.variable != base.variable:
+        parts.append("literal" if w.variable == 0 else "regularised")
+    if w.s != base.s:
+        parts.append(f"s{w.s}")
+    if w.substeps != base.substeps:
+        parts.append(f"k{w.substeps}" if w.substeps else "kauto")
+    return "_".join(parts)
 
 
 def _config(w, args, world):
@@ -439,12 +451,32 @@ def main() -> int:
                     help="outer steps per solve (default: the workload's); for profiling runs")
     ap.add_argument("--cpu-sample-steps", type=int, default=150)
     ap.add_argument("--ref-sample-steps", type=int, default=40)
+    ap.add_argument("--variable", choices=["regularised", "literal"], default=None,
+                    help="angular variable (default: the workload's); the literal variable "
+                         "needs more substeps, see --substeps")
+    ap.add_argument("--spin-weight", type=int, default=None,
+                    help="spin weight s (default: the workload's -2; 0 is the scalar field)")
+    ap.add_argument("--substeps", type=int, default=None,
+                    help="Lax-Wendroff steps per outer step (default: the workload's; 0: from "
+                         "the stability bound)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
+    if w is not None:
+        if args.variable is not None:
+            w = w.with_(variable=1 if args.variable == "regularised" else 0)
+        if args.spin_weight is not None:
+            w = w.with_(s=args.spin_weight)
+        if args.substeps is not None:
+            w = w.with_(substeps=args.substeps)
+        if w != WORKLOADS[args.workload]:
+            w = w.with_(name=_variant_name(w, WORKLOADS[args.workload]))
     if args.impl == "reference":
-        return run_reference(args, w or batched_instances()[2])
+        w = w or batched_instances()[2]
+        if w.substeps == 0:
+            raise SystemExit("the oracle takes an explicit number of substeps (--substeps k)")
+        return run_reference(args, w)
 
     import torch
     import paper_1010_3816_gb300 as tk
@@ -463,13 +495,16 @@ def main() -> int:
             dist.destroy_process_group()
         return rc
     n_outer = args.outer_steps or w.steps
-    updates = w.points * n_outer * w.substeps
-    launches_per_solve = 3 + n_outer * w.substeps + len(w.observers)
-
     stream = torch.cuda.current_stream()
     solver = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
                        substeps=w.substeps, variable=w.variable, precision=args.precision,
                        stream=stream.cuda_stream)
+    if w.substeps == 0:
+        # substeps chosen by the solver's stability bound at the precompute
+        solver.precompute(w.a, w.M, w.s, w.m)
+        w = w.with_(substeps=solver.substeps)
+    updates = w.points * n_outer * w.substeps
+    launches_per_solve = 3 + n_outer * w.substeps + len(w.observers)
     re, im = initial_planes(w)
     d_re = torch.from_numpy(re).cuda()
     d_im = torch.from_numpy(im).cuda()
@@ -526,7 +561,7 @@ def main() -> int:
     kern_s = statistics.mean(step_ms) * 1e-3 / (n_outer * w.substeps)   # per launch
     pts = w.points
     f_clk = (clk.get("sm_mhz") or 2070.0) * 1e6
-    traffic, traffic_src = MEASURED_TRAFFIC.get((args.workload, args.precision), (None, None))
+    traffic, traffic_src = MEASURED_TRAFFIC.get((w.name, args.precision), (None, None))
     if args.precision == 0:
         achieved = FP64_FLOP_PER_UPDATE * pts / kern_s / 1e12
         peak = NUM_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * f_clk / 1e12

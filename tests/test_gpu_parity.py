@@ -112,6 +112,24 @@ def test_kerr_25601x64_full_grid_first_steps():
     print(res)
 
 
+def test_schwarzschild_1601x32_literal_variable():
+    """The 1601 x 32 workload in the literal variable Phi with the sin^2 data
+    taken literally (not regular at theta = pi for s = -2, m = 2), four
+    Lax-Wendroff steps per outer step (the literal pole stiffness needs
+    dt <= dr*/8), 400 outer steps; held to the conditioned bar."""
+    w = SCHWARZSCHILD_1601x32.with_(variable=0, substeps=4, steps=400)
+    ref = run_oracle(w)
+    res = compare(w, run_gpu(w), ref, perturbed=sensitivity(w))
+    print(res)
+
+
+def test_kerr_25601x64_scalar_field_first_steps():
+    """The scalar field (s = 0) on the full 25601 x 64 Kerr grid, 120 steps."""
+    w = KERR_25601x64.with_(s=0)
+    res = compare(w, run_gpu(w, steps=120), run_oracle(w, steps=120))
+    print(res)
+
+
 def test_kerr_25601x64_full_length_properties():
     """All 38400 steps of the 25601 x 64 Kerr workload: finite, waveform of the
     right length, and exact a -> -a conjugation on the full run."""
