@@ -209,6 +209,15 @@ tk_status tk_set_state(tk_solver *S, const double *planes4, int on_device);
 tk_status tk_stability_bound(tk_solver *S, double growth_per_step, double *dt_max,
                              int *substeps_needed);
 
+/* Lax-Wendroff steps per kernel launch: 1, 2, or 0 for the default (2 for
+ * TK_PREC_F32, whose step is bound by memory traffic, 1 for TK_PREC_F64,
+ * whose step is bound by FP64 arithmetic).  With 2, pairs of inner steps run
+ * in one launch that reads the state and the coefficient tables once; each
+ * warp recomputes the intermediate level one column beyond its range, which
+ * adds arithmetic but no DRAM traffic.  Results are bit-identical either way.
+ * Returns TK_ERR_ARG for other values. */
+tk_status tk_set_steps_per_launch(tk_solver *S, int steps);
+
 /* Lax-Wendroff steps per outer step in use (the count chosen at the last
  * tk_precompute_coeffs when the grid was made with substeps = 0). */
 tk_status tk_get_substeps(const tk_solver *S, int *substeps);

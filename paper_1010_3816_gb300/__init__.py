@@ -31,7 +31,8 @@ EXPORTS = ("tk_make_grid", "tk_precompute_coeffs", "tk_set_initial_data", "tk_ad
            "tk_check_finite", "tk_synchronize", "tk_last_error", "tk_destroy", "tk_set_graph_chunk",
            "tk_batch_create", "tk_batch_step", "tk_batch_tune", "tk_batch_set_segment",
            "tk_batch_set_graph_chunk", "tk_batch_info", "tk_batch_last_error", "tk_batch_destroy",
-           "tk_extract_noalloc", "tk_adjoint", "tk_set_initial_gaussian", "tk_get_substeps")
+           "tk_extract_noalloc", "tk_adjoint", "tk_set_initial_gaussian", "tk_get_substeps",
+           "tk_set_steps_per_launch")
 
 
 class TkError(RuntimeError):
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH):
             "tk_set_initial_gaussian": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double,
                                                   C.c_double, C.c_uint64]),
             "tk_get_substeps": (C.c_int, [_vp, _ip]),
+            "tk_set_steps_per_launch": (C.c_int, [_vp, C.c_int]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -245,6 +247,10 @@ def tk_get_substeps(h) -> int:
     return v.value
 
 
+def tk_set_steps_per_launch(h, steps: int) -> None:
+    _check(h, load_library().tk_set_steps_per_launch(h, int(steps)))
+
+
 def tk_set_graph_chunk(h, outer_steps: int) -> None:
     _check(h, load_library().tk_set_graph_chunk(h, int(outer_steps)))
 
@@ -369,6 +375,10 @@ class Solver:
 
     def set_graph_chunk(self, outer_steps: int):
         tk_set_graph_chunk(self.h, outer_steps)
+        return self
+
+    def set_steps_per_launch(self, steps: int):
+        tk_set_steps_per_launch(self.h, steps)
         return self
 
     def stability_bound(self, growth_per_step: float = 2.5e-5):

@@ -101,6 +101,8 @@ void fill_launch(const tk_solver *S, tk::StepLaunch &L)
     L.NP = S->NP;
     L.blocks = S->blocks;
     L.warps = S->warps;
+    L.fused = 0;
+    L.obs_mask = 0;
     L.dt_inner = S->dt / S->substeps;
     L.half = S->half;
     L.node = S->node;
@@ -179,6 +181,10 @@ tk_status tk_make_grid(tk_solver **out, double rstar_min, double rstar_max, int 
     S->dt = dt;
     S->blocks = tk::step_grid_shape(precision, S->K, Nr, S->num_sms, &S->warps);
     S->adj_blocks = tk::adjoint_grid_shape(precision, S->K, Nr, S->num_sms, &S->adj_warps);
+    S->fused_blocks = tk::fused_grid_shape(precision, S->K, Nr, S->num_sms, &S->fused_warps);
+    // two steps per launch where the step is bound by memory (FP32); the FP64
+    // step is bound by its arithmetic, which the two-step kernel's overlap adds to
+    S->fuse = (precision == TK_PREC_F32);
 
     const size_t se = state_elems(S);
     tk_status st = TK_OK;
@@ -357,35 +363,57 @@ tk_status tk_add_observer(tk_solver *S, double rstar_obs, double theta_obs, int 
 }
 
 // Enqueue `outer` outer steps starting from level `cur` on stream `st`;
-// returns the level holding the result.
+// returns the level holding the result.  Inner steps run one per launch, or
+// in pairs through the two-step kernel when S->fuse; an outer step that ends
+// inside a pair is observed there (obs_mask).  Calls start on an outer-step
+// boundary, so the inner index t counts from one.
 static cudaError_t enqueue_steps(const tk_solver *S, int cur, int outer, cudaStream_t st, int *cur_out)
 {
     tk::StepLaunch L;
     tkh::fill_launch(S, L);
-    for (int it = 0; it < outer; ++it)
-        for (int k = 0; k < S->substeps; ++k) {
-            L.u_in = S->u[cur];
-            L.u_out = S->u[cur ^ 1];
-            L.write_wave = (k == S->substeps - 1) && S->nobs > 0;
-            cudaError_t e = tk::launch_lw_step(L, st);
-            if (e != cudaSuccess) return e;
-            cur ^= 1;
+    const long long k = S->substeps, total = (long long)outer * k;
+    for (long long t = 0; t < total;) {
+        L.u_in = S->u[cur];
+        L.u_out = S->u[cur ^ 1];
+        if (S->fuse && t + 1 < total) {
+            L.fused = 1;
+            L.blocks = S->fused_blocks;
+            L.warps = S->fused_warps;
+            L.obs_mask = ((t + 1) % k == 0 ? 1 : 0) | ((t + 2) % k == 0 ? 2 : 0);
+            L.write_wave = L.obs_mask != 0 && S->nobs > 0;
+            t += 2;
+        } else {
+            L.fused = 0;
+            L.blocks = S->blocks;
+            L.warps = S->warps;
+            L.obs_mask = 0;
+            L.write_wave = (t + 1) % k == 0 && S->nobs > 0;
+            t += 1;
         }
+        cudaError_t e = tk::launch_lw_step(L, st);
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+    }
     *cur_out = cur;
     return cudaSuccess;
 }
 
+// Outer steps per captured graph: an even number of launches per replay keeps
+// the ping-pong level fixed, and with two-step launches the chunk holds whole
+// pairs (inner steps a multiple of four).
 static int graph_chunk(const tk_solver *S)
 {
+    int c;
     if (S->graph_chunk >= 0) {
-        // an even number of launches per replay keeps the ping-pong level fixed
-        int c = S->graph_chunk;
-        if (c > 0 && ((long long)c * S->substeps) % 2) ++c;
-        return c;
+        c = S->graph_chunk;
+        if (c == 0) return 0;
+    } else {
+        // automatic: about 64 launches per replay
+        const int per = S->fuse ? (S->substeps + 1) / 2 : S->substeps;
+        c = (64 + per - 1) / per;
     }
-    // automatic: about 64 launches per replay, rounded to an even launch count
-    int c = (64 + S->substeps - 1) / S->substeps;
-    if (((long long)c * S->substeps) % 2) ++c;
+    const int mult = S->fuse ? 4 : 2;
+    while (((long long)c * S->substeps) % mult) ++c;
     return c;
 }
 
@@ -447,6 +475,18 @@ tk_status tk_step(tk_solver *S, int n)
         S->count += n;
         S->steps_done += n;
     }
+    return TK_OK;
+}
+
+tk_status tk_set_steps_per_launch(tk_solver *S, int steps)
+{
+    tk_status st = enter(S);
+    if (st != TK_OK) return st;
+    if (steps < 0 || steps > 2)
+        return fail(S, TK_ERR_ARG, "tk_set_steps_per_launch: %d is not 0, 1 or 2", steps);
+    S->fuse_mode = steps;
+    S->fuse = steps == 0 ? (S->precision == TK_PREC_F32) : (steps == 2);
+    S->epoch++;
     return TK_OK;
 }
 

@@ -90,7 +90,9 @@ struct StepLaunch {
     int precision, K;
     int Nr, NP;
     int blocks;           // grid size (columns are split evenly over its warps)
-    int warps;            // warps per block (from step_grid_shape)
+    int warps;            // warps per block (from step_grid_shape or fused_grid_shape)
+    int fused;            // 1: two Lax-Wendroff steps in this launch (lw_step2_kernel)
+    int obs_mask;         // fused: bit 0, an outer step ends after the first step; bit 1, after the second
     double dt_inner;      // Lax-Wendroff step
     const void *u_in;
     void *u_out;
@@ -109,6 +111,8 @@ cudaError_t launch_lw_step(const StepLaunch &L, cudaStream_t st);
 // Launch shape of the step kernel for a grid: returns the number of blocks
 // and sets *warps to the warps per block.
 int step_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
+// Launch shape of the two-step kernel.
+int fused_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
 // Launch shape of the adjoint step kernel: returns the number of blocks and
 // sets *warps to the warps per block.
 int adjoint_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);

@@ -44,6 +44,10 @@ struct tk_solver {
     bool auto_k = false;        // substeps from the stability bound at each precompute
     int blocks = 1;             // step kernel launch shape
     int warps = 4;
+    int fuse = 0;               // 1: inner steps in pairs, one two-step launch per pair
+    int fuse_mode = 0;          // as set by tk_set_steps_per_launch (0: automatic)
+    int fused_blocks = 1;       // two-step kernel launch shape
+    int fused_warps = 4;
     int adj_blocks = 1;         // adjoint kernel launch shape
     int adj_warps = 4;
     // CUDA-graph replay of chunks of outer steps (0 = launch every step directly)

@@ -231,7 +231,7 @@ __device__ __forceinline__ void full_node(const T (&hm)[4][K], const T (&hp)[4][
 template <typename T, int K>
 __device__ __forceinline__ void observe(int i, int lane, const T (&o)[4][K], const ObsDev &obs,
                                         double *wave, int64_t cap, const long long *sample_ctr,
-                                        const double *w_row)
+                                        const double *w_row, int sample_offset = 0)
 {
     for (int k = 0; k < obs.n; ++k) {
         const int slot = (i == obs.i0[k]) ? 0 : ((i == obs.i0[k] + 1) ? 1 : -1);
@@ -258,7 +258,7 @@ __device__ __forceinline__ void observe(int i, int lane, const T (&o)[4][K], con
         }
         if (lane == 0) {
             const double wr = slot ? obs.wr1[k] : obs.wr0[k];
-            const long long sample = *(volatile const long long *)sample_ctr;
+            const long long sample = *(volatile const long long *)sample_ctr + sample_offset;
             double *dst = wave + ((size_t)k * cap + sample) * 4 + 2 * slot;
             dst[0] = wr * cr;
             dst[1] = wr * ci;

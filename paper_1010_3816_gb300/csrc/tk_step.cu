@@ -36,14 +36,14 @@ struct WaveArgs {
 // here, so the increment cannot race with a read of the same launch; the next
 // launch on the stream sees it.  Keeping the index on the device lets a
 // captured chunk of launches be replayed unchanged.
-__device__ __forceinline__ void advance_sample(const WaveArgs &wa)
+__device__ __forceinline__ void advance_sample(const WaveArgs &wa, int samples = 1)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned int prev = atomicAdd(wa.done, 1u);
         if (prev == gridDim.x - 1) {
-            atomicAdd((unsigned long long *)wa.sample, 1ull);
+            atomicAdd((unsigned long long *)wa.sample, (unsigned long long)samples);
             atomicExch(wa.done, 0u);
             __threadfence();
         }
@@ -147,6 +147,91 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
     if (wa.write) advance_sample(wa);
 }
 
+// Two Lax-Wendroff steps per launch, u^n -> u^{n+2}, for the HBM-bound
+// precision: state and tables cross DRAM once per two steps.  A warp owns the
+// output columns [i0, i1) of the same split as the one-step kernel and
+// recomputes the intermediate level u^{n+1} on [i0 - 1, i1], one column
+// beyond each end, so warps need nothing from each other.  It loads u^n_p for
+// p = i0 - 2 .. i1 + 1 and runs four lagged stages per p: the level-1 half
+// node p - 1/2, the level-1 node p - 1, the level-2 half node p - 3/2 and the
+// level-2 node p - 2.  The tables of a column are read twice, one column
+// apart, the second time from cache.  Every node and half node does the
+// arithmetic of the one-step kernel on the same operands, so two fused steps
+// are bit-identical to two one-step launches.  obs_mask bit 0: an outer step
+// ends after the first of the two steps; bit 1: after the second.
+template <typename T, int K>
+constexpr int fused_warps()
+{
+    return sizeof(T) == 8 ? (K == 1 ? 20 : K == 2 ? 8 : 4) : (K == 1 ? 32 : K == 2 ? 16 : 8);
+}
+
+template <typename T, int K, int W>
+__global__ void __launch_bounds__(W * 32, fused_warps<T, K>() / W)
+lw_step2_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__restrict__ half,
+                const T *__restrict__ node, int Nr, T eh, T en, const WaveArgs wa, int obs_mask)
+{
+    constexpr int NP = 32 * K;
+    constexpr size_t SP = 4 * NP, HP = (size_t)kNCH * NP, NQ = (size_t)kNCN * NP;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int i0, i1, left;
+    warp_range<W>(Nr, wib, &i0, &i1, &left);
+    const int row = lane * K;
+    const int second = obs_mask & 1;   // sample offset of the level-2 observation
+    if (i1 > i0) {
+        T a0[4][K], h1m[4][K], u1m[4][K], h2m[4][K];
+        zero_col<T, K>(a0);
+        zero_col<T, K>(h1m);
+        zero_col<T, K>(u1m);
+        zero_col<T, K>(h2m);
+        for (int p = i0 - 2; p <= i1 + 1; ++p) {
+            T c0[4][K], h1p[4][K], u1c[4][K], h2p[4][K];
+            if (p >= 0 && p < Nr) load_col<T, K>(u_in + (size_t)p * SP + row, c0);
+            else zero_col<T, K>(c0);
+            // level 1, half node between p - 1 and p
+            if (p >= i0 - 1 && p >= 1 && p < Nr)
+                half_node<T, K>(a0, c0, half + (size_t)(p - 1) * HP + row, eh, h1p);
+            else
+                zero_col<T, K>(h1p);
+            // level 1, node q = p - 1 (zero on the radial edges and outside the grid)
+            const int q = p - 1;
+            if (p >= i0 && q >= 1 && q <= Nr - 2)
+                full_node<T, K>(h1m, h1p, a0, node + (size_t)q * NQ + row, en, u1c);
+            else
+                zero_col<T, K>(u1c);
+            if ((obs_mask & 1) && q >= i0 && q < i1)
+                observe<T, K>(q, lane, u1c, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, 0);
+            // level 2, half node between r = p - 2 and p - 1
+            const int r = p - 2;
+            if (p >= i0 + 1 && r >= 0 && r + 1 < Nr)
+                half_node<T, K>(u1m, u1c, half + (size_t)r * HP + row, eh, h2p);
+            else
+                zero_col<T, K>(h2p);
+            // level 2, node r
+            if (p >= i0 + 2) {
+                T o[4][K];
+                if (r >= 1 && r <= Nr - 2)
+                    full_node<T, K>(h2m, h2p, u1m, node + (size_t)r * NQ + row, en, o);
+                else
+                    zero_col<T, K>(o);
+                store_col<T, K>(u_out + (size_t)r * SP + row, o);
+                if (obs_mask & 2)
+                    observe<T, K>(r, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, second);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    a0[c][t] = c0[c][t];
+                    h1m[c][t] = h1p[c][t];
+                    u1m[c][t] = u1c[c][t];
+                    h2m[c][t] = h2p[c][t];
+                }
+        }
+    }
+    if (obs_mask) advance_sample(wa, (obs_mask & 1) + ((obs_mask >> 1) & 1));
+}
+
 template <typename T, int K, int W>
 constexpr size_t step_smem_bytes()
 {
@@ -175,6 +260,25 @@ cudaError_t launch_shape(const StepLaunch &L, const WaveArgs &wa, cudaStream_t s
 }
 
 template <typename T, int K>
+cudaError_t launch_fused(const StepLaunch &L, const WaveArgs &wa, cudaStream_t st)
+{
+    constexpr int WF = fused_warps<T, K>();
+    const T eh = (T)(0.25 * L.dt_inner), en = (T)(0.5 * L.dt_inner);
+    const int mask = L.write_wave ? L.obs_mask : 0;
+    if (L.warps == WF)
+        lw_step2_kernel<T, K, WF><<<L.blocks, WF * 32, 0, st>>>(
+            (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node, L.Nr, eh, en, wa,
+            mask);
+    else if (L.warps == kNarrowWarps)
+        lw_step2_kernel<T, K, kNarrowWarps><<<L.blocks, kNarrowWarps * 32, 0, st>>>(
+            (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node, L.Nr, eh, en, wa,
+            mask);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template <typename T, int K>
 cudaError_t launch_typed(const StepLaunch &L, cudaStream_t st)
 {
     WaveArgs wa;
@@ -185,6 +289,7 @@ cudaError_t launch_typed(const StepLaunch &L, cudaStream_t st)
     wa.wave = L.wave;
     wa.w_row = L.w_row;
     wa.obs = L.obs;
+    if (L.fused) return launch_fused<T, K>(L, wa, st);
     if (L.warps == wide_warps<T, K>()) return launch_shape<T, K, wide_warps<T, K>()>(L, wa, st);
     if (L.warps == kNarrowWarps) return launch_shape<T, K, kNarrowWarps>(L, wa, st);
     return cudaErrorInvalidValue;
@@ -221,7 +326,36 @@ int grid_shape(int Nr, int num_sms, int *warps)
     return blocks < 1 ? 1 : blocks;
 }
 
+template <typename T, int K>
+int fused_shape(int Nr, int num_sms, int *warps)
+{
+    constexpr int WF = fused_warps<T, K>();
+    if ((long long)Nr >= (long long)num_sms * WF) {
+        *warps = WF;
+        return num_sms;
+    }
+    *warps = kNarrowWarps;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_step2_kernel<T, K, kNarrowWarps>,
+                                                      kNarrowWarps * 32, 0) != cudaSuccess || n < 1)
+        n = 1;
+    int blocks = num_sms * n;
+    if (blocks > Nr / kNarrowWarps) blocks = Nr / kNarrowWarps;
+    return blocks < 1 ? 1 : blocks;
+}
+
 }  // namespace
+
+int fused_grid_shape(int precision, int K, int Nr, int num_sms, int *warps)
+{
+    if (precision == 0)
+        return K == 1 ? fused_shape<double, 1>(Nr, num_sms, warps)
+             : K == 2 ? fused_shape<double, 2>(Nr, num_sms, warps)
+                      : fused_shape<double, 4>(Nr, num_sms, warps);
+    return K == 1 ? fused_shape<float, 1>(Nr, num_sms, warps)
+         : K == 2 ? fused_shape<float, 2>(Nr, num_sms, warps)
+                  : fused_shape<float, 4>(Nr, num_sms, warps);
+}
 
 int step_grid_shape(int precision, int K, int Nr, int num_sms, int *warps)
 {

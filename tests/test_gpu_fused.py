@@ -1,0 +1,98 @@
+"""Two Lax-Wendroff steps per launch (tk_set_steps_per_launch).
+
+The two-step kernel does, per node and half node, the arithmetic of the
+one-step kernel on the same operands, so a solve with pairs of steps per
+launch must be bit-identical to the same solve one step per launch: state and
+waveforms, for every theta packing, both launch shapes (one block per SM on
+large grids, small blocks on small ones), odd and even numbers of substeps
+(an outer step may end inside a pair), odd step counts (a single launch ends
+the call), observers on the radial edge columns, and graph replay.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from inputs import Workload, initial_planes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_1010_3816_gb300 as tk
+    tk.load_library()
+
+
+def _run(w, precision, steps_per_launch, calls, chunk=-1):
+    import paper_1010_3816_gb300 as tk
+    g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
+                  substeps=w.substeps, variable=w.variable, precision=precision)
+    g.precompute(w.a, w.M, w.s, w.m)
+    g.set_steps_per_launch(steps_per_launch)
+    g.set_graph_chunk(chunk)
+    re, im = initial_planes(w)
+    g.set_initial(re, im)
+    ids = [g.add_observer(r, t) for r, t in w.observers]
+    for n in calls:
+        g.step(n)
+    out = g.state(), [g.waveform(k) for k in ids]
+    g.close()
+    return out
+
+
+def _grid(Nr, Ntheta, **kw):
+    drs = 1.0 / 16.0
+    rs_min = -30.0
+    rs_max = rs_min + (Nr - 1) * drs
+    base = dict(name=f"f{Nr}x{Ntheta}", a=0.9, m=2, rs_min=rs_min, rs_max=rs_max, Nr=Nr,
+                Ntheta=Ntheta, dt=drs / 2, center=5.0, width=3.0, noise=1e-3, seed=7,
+                observers=((rs_min, math.pi / 2), (rs_max, 1.0), (rs_min + 17.3 * drs * 16, 2.0)))
+    base.update(kw)
+    return Workload(**base)
+
+
+CASES = [
+    # precision, workload (sizes pick the launch shape), calls of tk_step
+    (1, _grid(3001, 64, substeps=2), (7, 10, 1)),          # FP32 K=2, one block per SM
+    (1, _grid(3001, 64, substeps=1), (9, 4)),              # an outer step ends inside every pair
+    (1, _grid(5003, 32, substeps=3), (5, 6)),              # FP32 K=1, pairs straddle outer steps
+    (1, _grid(1301, 128, substeps=4), (3, 8)),             # FP32 K=4
+    (1, _grid(401, 64, substeps=2), (13,)),                # small grid: small blocks
+    (0, _grid(1301, 64, substeps=2), (7, 6)),              # FP64 K=2 one block per SM
+    (0, _grid(3101, 32, substeps=3, variable=0, dt=0.01), (5, 4)),  # FP64 K=1, literal
+    (0, _grid(700, 128, substeps=1), (11,)),               # FP64 K=4
+]
+
+
+@pytest.mark.parametrize("precision,w,calls", CASES, ids=[f"case{k}" for k in range(len(CASES))])
+def test_two_steps_per_launch_bit_identical(precision, w, calls):
+    s1, w1 = _run(w, precision, 1, calls)
+    s2, w2 = _run(w, precision, 2, calls)
+    assert np.isfinite(s1).all()
+    assert np.array_equal(s1, s2)
+    assert all(np.array_equal(a, b) for a, b in zip(w1, w2))
+    # graph chunks of other lengths (direct launches for the remainder)
+    s3, w3 = _run(w, precision, 2, calls, chunk=3)
+    assert np.array_equal(s1, s3)
+    assert all(np.array_equal(a, b) for a, b in zip(w1, w3))
+
+
+def test_fp32_pairs_steps_by_default():
+    w = _grid(3001, 64, substeps=2)
+    s0, w0 = _run(w, 1, 0, (6,))
+    s2, w2 = _run(w, 1, 2, (6,))
+    assert np.array_equal(s0, s2) and all(np.array_equal(a, b) for a, b in zip(w0, w2))
+
+
+def test_steps_per_launch_argument():
+    import paper_1010_3816_gb300 as tk
+    w = _grid(401, 32)
+    g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt)
+    for bad in (-1, 3):
+        with pytest.raises(tk.TkError):
+            g.set_steps_per_launch(bad)
+    g.close()
