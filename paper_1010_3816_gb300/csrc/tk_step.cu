@@ -232,6 +232,146 @@ lw_step2_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__re
     if (obs_mask) advance_sample(wa, (obs_mask & 1) + ((obs_mask >> 1) & 1));
 }
 
+// The two-step sweep with its loads staged through shared memory.  Per warp
+// a ring of three slots, each one column's state (4 planes) and tables (11 +
+// 10 entries): while the warp computes column p from slot p % 3 (level 1)
+// and slot (p - 1) % 3 (level 2, the same tables one column later), the
+// copies of column p + 1 into the third slot are in flight (cp.async, one
+// group per column; a lane copies and reads only its own rows, so
+// cp.async.wait_group is the only synchronisation).  DRAM is read once per
+// column and the load latency of column p + 1 overlaps the arithmetic of
+// column p.  The arithmetic is that of lw_step2_kernel.
+constexpr int kRingSlots = 3;
+constexpr int kSlotCols = 4 + kNCH + kNCN;   // state, half-node table, node table
+
+template <typename T, int K>
+constexpr int ring_warps()
+{
+    return K == 1 ? 20 : K == 2 ? 8 : 4;
+}
+
+template <typename T, int K>
+constexpr size_t ring_smem_bytes()
+{
+    return (size_t)ring_warps<T, K>() * kRingSlots * kSlotCols * 32 * K * sizeof(T);
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem), "n"(BYTES)
+                     : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Issue the copies of column p (state u_p, tables half_{p-1}, node_{p-1}, the
+// level-1 operands at step p of the sweep) into `slot`, then commit a group
+// (empty where the column is outside the grid).
+template <typename T, int K>
+__device__ __forceinline__ void ring_fetch(T *slot, const T *__restrict__ u, const T *__restrict__ half,
+                                           const T *__restrict__ node, int p, int Nr, int row)
+{
+    constexpr int NP = 32 * K, B = K * (int)sizeof(T);
+    if (p >= 0 && p < Nr) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cp_async<B>(slot + c * NP + row, u + ((size_t)p * 4 + c) * NP + row);
+    }
+    if (p >= 1 && p < Nr) {
+#pragma unroll
+        for (int q = 0; q < kNCH; ++q)
+            cp_async<B>(slot + (4 + q) * NP + row, half + ((size_t)(p - 1) * kNCH + q) * NP + row);
+#pragma unroll
+        for (int q = 0; q < kNCN; ++q)
+            cp_async<B>(slot + (4 + kNCH + q) * NP + row, node + ((size_t)(p - 1) * kNCN + q) * NP + row);
+    }
+    cp_async_commit();
+}
+
+template <typename T, int K, int W>
+__global__ void __launch_bounds__(W * 32, 1)
+lw_step2_ring_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__restrict__ half,
+                     const T *__restrict__ node, int Nr, T eh, T en, const WaveArgs wa, int obs_mask)
+{
+    constexpr int NP = 32 * K;
+    constexpr size_t SP = 4 * NP;
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    T *ring = reinterpret_cast<T *>(sh_raw) + (size_t)wib * kRingSlots * kSlotCols * NP;
+    int i0, i1, left;
+    warp_range<W>(Nr, wib, &i0, &i1, &left);
+    const int row = lane * K;
+    const int second = obs_mask & 1;
+    if (i1 > i0) {
+        T a0[4][K], h1m[4][K], u1m[4][K], h2m[4][K];
+        zero_col<T, K>(a0);
+        zero_col<T, K>(h1m);
+        zero_col<T, K>(u1m);
+        zero_col<T, K>(h2m);
+        ring_fetch<T, K>(ring, u_in, half, node, i0 - 2, Nr, row);
+        int cur = 0;
+        for (int p = i0 - 2; p <= i1 + 1; ++p) {
+            const int nxt = cur == kRingSlots - 1 ? 0 : cur + 1;
+            const int prv = cur == 0 ? kRingSlots - 1 : cur - 1;
+            if (p + 1 <= i1 + 1)
+                ring_fetch<T, K>(ring + nxt * kSlotCols * NP, u_in, half, node, p + 1, Nr, row);
+            else
+                cp_async_commit();
+            cp_async_wait_one();
+            const T *sc = ring + cur * kSlotCols * NP;    // column p: u_p, half_{p-1}, node_{p-1}
+            const T *sp = ring + prv * kSlotCols * NP;    // column p - 1: half_{p-2}, node_{p-2}
+            T c0[4][K], h1p[4][K], u1c[4][K], h2p[4][K];
+            if (p >= 0 && p < Nr) load_col<T, K>(sc + row, c0);
+            else zero_col<T, K>(c0);
+            if (p >= i0 - 1 && p >= 1 && p < Nr)
+                half_node<T, K>(a0, c0, sc + 4 * NP + row, eh, h1p);
+            else
+                zero_col<T, K>(h1p);
+            const int q = p - 1;
+            if (p >= i0 && q >= 1 && q <= Nr - 2)
+                full_node<T, K>(h1m, h1p, a0, sc + (4 + kNCH) * NP + row, en, u1c);
+            else
+                zero_col<T, K>(u1c);
+            if ((obs_mask & 1) && q >= i0 && q < i1)
+                observe<T, K>(q, lane, u1c, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, 0);
+            const int r = p - 2;
+            if (p >= i0 + 1 && r >= 0 && r + 1 < Nr)
+                half_node<T, K>(u1m, u1c, sp + 4 * NP + row, eh, h2p);
+            else
+                zero_col<T, K>(h2p);
+            if (p >= i0 + 2) {
+                T o[4][K];
+                if (r >= 1 && r <= Nr - 2)
+                    full_node<T, K>(h2m, h2p, u1m, sp + (4 + kNCH) * NP + row, en, o);
+                else
+                    zero_col<T, K>(o);
+                store_col<T, K>(u_out + (size_t)r * SP + row, o);
+                if (obs_mask & 2)
+                    observe<T, K>(r, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, second);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    a0[c][t] = c0[c][t];
+                    h1m[c][t] = h1p[c][t];
+                    u1m[c][t] = u1c[c][t];
+                    h2m[c][t] = h2p[c][t];
+                }
+            cur = nxt;
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    if (obs_mask) advance_sample(wa, (obs_mask & 1) + ((obs_mask >> 1) & 1));
+}
+
 template <typename T, int K, int W>
 constexpr size_t step_smem_bytes()
 {
@@ -259,23 +399,52 @@ cudaError_t launch_shape(const StepLaunch &L, const WaveArgs &wa, cudaStream_t s
     return cudaGetLastError();
 }
 
+template <typename T, int K, int W>
+cudaError_t ring_smem_setup()
+{
+    static cudaError_t e = cudaFuncSetAttribute(
+        lw_step2_ring_kernel<T, K, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)(ring_smem_bytes<T, K>() / ring_warps<T, K>() * W));
+    return e;
+}
+
+template <typename T, int K, int W>
+cudaError_t launch_ring(const StepLaunch &L, const WaveArgs &wa, T eh, T en, int mask, cudaStream_t st)
+{
+    cudaError_t e = ring_smem_setup<T, K, W>();
+    if (e != cudaSuccess) return e;
+    const size_t smem = ring_smem_bytes<T, K>() / ring_warps<T, K>() * W;
+    lw_step2_ring_kernel<T, K, W><<<L.blocks, W * 32, smem, st>>>(
+        (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node, L.Nr, eh, en, wa, mask);
+    return cudaGetLastError();
+}
+
+// Two-step launch: the shared-memory ring kernel for FP32 (memory-bound), the
+// register-only kernel for FP64.
 template <typename T, int K>
 cudaError_t launch_fused(const StepLaunch &L, const WaveArgs &wa, cudaStream_t st)
 {
-    constexpr int WF = fused_warps<T, K>();
     const T eh = (T)(0.25 * L.dt_inner), en = (T)(0.5 * L.dt_inner);
     const int mask = L.write_wave ? L.obs_mask : 0;
-    if (L.warps == WF)
-        lw_step2_kernel<T, K, WF><<<L.blocks, WF * 32, 0, st>>>(
-            (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node, L.Nr, eh, en, wa,
-            mask);
-    else if (L.warps == kNarrowWarps)
-        lw_step2_kernel<T, K, kNarrowWarps><<<L.blocks, kNarrowWarps * 32, 0, st>>>(
-            (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node, L.Nr, eh, en, wa,
-            mask);
-    else
+    if constexpr (sizeof(T) == 4) {
+        constexpr int WR = ring_warps<T, K>();
+        if (L.warps == WR) return launch_ring<T, K, WR>(L, wa, eh, en, mask, st);
+        if (L.warps == kNarrowWarps) return launch_ring<T, K, kNarrowWarps>(L, wa, eh, en, mask, st);
         return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    } else {
+        constexpr int WF = fused_warps<T, K>();
+        if (L.warps == WF)
+            lw_step2_kernel<T, K, WF><<<L.blocks, WF * 32, 0, st>>>(
+                (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node, L.Nr, eh, en,
+                wa, mask);
+        else if (L.warps == kNarrowWarps)
+            lw_step2_kernel<T, K, kNarrowWarps><<<L.blocks, kNarrowWarps * 32, 0, st>>>(
+                (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node, L.Nr, eh, en,
+                wa, mask);
+        else
+            return cudaErrorInvalidValue;
+        return cudaGetLastError();
+    }
 }
 
 template <typename T, int K>
@@ -329,16 +498,25 @@ int grid_shape(int Nr, int num_sms, int *warps)
 template <typename T, int K>
 int fused_shape(int Nr, int num_sms, int *warps)
 {
-    constexpr int WF = fused_warps<T, K>();
+    constexpr int WF = sizeof(T) == 4 ? ring_warps<T, K>() : fused_warps<T, K>();
     if ((long long)Nr >= (long long)num_sms * WF) {
         *warps = WF;
         return num_sms;
     }
     *warps = kNarrowWarps;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_step2_kernel<T, K, kNarrowWarps>,
-                                                      kNarrowWarps * 32, 0) != cudaSuccess || n < 1)
-        n = 1;
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+        e = ring_smem_setup<T, K, kNarrowWarps>();
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &n, lw_step2_ring_kernel<T, K, kNarrowWarps>, kNarrowWarps * 32,
+                ring_smem_bytes<T, K>() / ring_warps<T, K>() * kNarrowWarps);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_step2_kernel<T, K, kNarrowWarps>,
+                                                          kNarrowWarps * 32, 0);
+    }
+    if (e != cudaSuccess || n < 1) n = 1;
     int blocks = num_sms * n;
     if (blocks > Nr / kNarrowWarps) blocks = Nr / kNarrowWarps;
     return blocks < 1 ? 1 : blocks;

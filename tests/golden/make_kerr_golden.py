@@ -4,9 +4,15 @@ steps per outer step).  Calls only oracle/ and the shared input generator.
 
 Stored: both waveforms (every sample), the physical state Phi = w Phi^,
 Pi = w Pi^ on every 8th theta row and every 16th r* column, and the L2 norm of
-each full physical plane.  Takes about an hour on 8 cores.
+each full physical plane.  Takes about two hours on 6 cores.
 
-    python tests/golden/make_kerr_golden.py [threads]
+With --perturbed it writes kerr_25601x64_oracle_perturbed.npz instead: the same
+run from the real initial plane times 1 + 2.2e-16 * N(0, 1) (numpy's default
+generator, seed 12345), i.e. a change of about one ulp.  The difference of the
+two stored runs is the run's own conditioning, which sets the parity bar of
+the full-length test.
+
+    python tests/golden/make_kerr_golden.py [threads] [--perturbed]
 """
 import math
 import os
@@ -26,14 +32,22 @@ ROWS = slice(0, None, 8)
 COLS = slice(0, None, 16)
 
 
+EPS = 2.2e-16
+SEED = 12345
+
+
 def main():
-    if len(sys.argv) > 1:
-        oracle.set_threads(int(sys.argv[1]))
+    args = [a for a in sys.argv[1:] if not a.startswith("--")]
+    perturbed = "--perturbed" in sys.argv
+    if args:
+        oracle.set_threads(int(args[0]))
     w = KERR_25601x64
     sol = oracle.Solver(M=w.M, a=w.a, s=w.s, m=w.m, rs_min=w.rs_min, rs_max=w.rs_max, Nr=w.Nr,
                         Ntheta=w.Ntheta, dt=w.dt, substeps=w.substeps, variable=w.variable)
     ids = [sol.add_observer(r, t) for r, t in w.observers]
     re, im = initial_planes(w)
+    if perturbed:
+        re = re * (1.0 + EPS * np.random.default_rng(SEED).standard_normal(re.shape))
     sol.set_initial(re, im)
     t0 = time.time()
     chunk = 1200
@@ -45,11 +59,12 @@ def main():
     wt = np.array([oracle.weight(w.s, w.m, w.variable, t) for t in th])[None, :, None]
     phys = st * wt
     np.savez_compressed(
-        os.path.join(HERE, "kerr_25601x64_oracle.npz"),
+        os.path.join(HERE, "kerr_25601x64_oracle" + ("_perturbed" if perturbed else "") + ".npz"),
         wave0=sol.waveform(ids[0]), wave1=sol.waveform(ids[1]),
         state_sub=phys[:, ROWS, COLS], plane_norms=np.linalg.norm(phys.reshape(4, -1), axis=1),
         rows=np.arange(w.Ntheta)[ROWS], cols=np.arange(w.Nr)[COLS],
-        note=np.array("oracle full run of " + w.name + f", {w.substeps} LW steps per outer step"))
+        note=np.array("oracle full run of " + w.name + f", {w.substeps} LW steps per outer step"
+                      + (f", real initial plane times 1 + {EPS} N(0,1), seed {SEED}" if perturbed else "")))
 
 
 if __name__ == "__main__":
