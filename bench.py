@@ -47,6 +47,10 @@ WORKLOADS = {"kerr": KERR_25601x64, "schwarzschild": SCHWARZSCHILD_1601x32,
 # 24 FMAs; an FMA counts 2 flops.
 FP64_FLOP_PER_UPDATE = (4 + 4 + 2 * 20) + (4 + 2 * 24)          # = 100
 FP64_INSTR_PER_UPDATE = 28 + 28
+# adjoint step per update: 50 FMAs + 6 multiplies + 6 adds (transposed blocks
+# and transposed theta couplings at the node and the half node)
+ADJ_FLOP_PER_UPDATE = 2 * 50 + 6 + 6                             # = 112
+ADJ_INSTR_PER_UPDATE = 62
 STATE_BYTES_PER_UPDATE = {0: 64, 1: 32}                         # read u^n, write u^{n+1}
 TABLE_BYTES_PER_UPDATE = {0: 21 * 8, 1: 21 * 4}                 # 11 + 10 table entries
 NUM_SMS = 152
@@ -61,6 +65,8 @@ FP32_FMA_PER_CLK_PER_SM = 128
 MEASURED_TRAFFIC = {
     ("kerr_a0.9_25601x64_38400steps", 0): (333.902592e6 + 38.241280e6,
                                            "profiles/lw_step_f64_kerr_25601x64.md"),
+    ("kerr_a0.9_25601x64_38400steps", 1): (194.818304e6 + 15.622144e6,
+                                           "profiles/lw_step2_ring_f32_kerr_25601x64.md"),
 }
 L2_FLUSH_BYTES = 256 << 20          # twice the 129 MB L2
 
@@ -244,6 +250,8 @@ def run_batched(args, tk, torch, rank, world, local):
     instances one after another through tk_step."""
     from paper_1010_3816_gb300 import distributed as D
     inst_all = batched_instances()
+    if args.instances:
+        inst_all = inst_all[:args.instances]
     n_outer = args.outer_steps or 500
     mine = D.shard([w.points * w.substeps for w in inst_all], rank, world)
     inst = [inst_all[k] for k in mine]
@@ -327,7 +335,7 @@ def run_batched(args, tk, torch, rank, world, local):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "batched_24_instances", "instances": len(inst_all),
+            "config": {"workload": f"batched_{len(inst_all)}_instances", "instances": len(inst_all),
                        "instances_on_rank0": len(inst), "outer_steps": n_outer,
                        "outer_steps_of_full_run": inst_all[0].steps,
                        "substeps_by_Ntheta": {"32": 2, "64": 4, "128": 8}, "ticks_per_outer_step": info["kmax"],
@@ -417,6 +425,20 @@ def run_adjoint(args, tk, torch, rank, world, local):
     value = 2 * inner * args.steps / (ms * 1e-3)
     fwd = statistics.mean(a.elapsed_time(b) for a, b in ev_f) * 1e-3
     bwd = statistics.mean(a.elapsed_time(b) for a, b in ev_b) * 1e-3
+    f_clk = (clk.get("sm_mhz") or 2070.0) * 1e6
+    peak = NUM_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * f_clk / 1e12
+    n_inner = n_outer * w.substeps
+
+    def fp64_roof(kernel, flop, instr, seconds):
+        launch_s = seconds / n_inner
+        ach = flop * w.points / launch_s / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": kernel, "flop_per_update": flop,
+                "fp64_issue_frac": instr * w.points / launch_s /
+                (NUM_SMS * FP64_FMA_PER_CLK_PER_SM * f_clk),
+                "launch_us": launch_s * 1e6,
+                "peak_source": "152 SMs x 2 DFMA/clk (measured) x 2 flop x median SM clock "
+                               f"{f_clk / 1e6:.0f} MHz"}
     if rank == 0:
         line = {
             "metric": "grid-point updates/s (forward + adjoint)", "value": value, "unit": "updates/s",
@@ -429,8 +451,12 @@ def run_adjoint(args, tk, torch, rank, world, local):
                        "gradient_wrt": ["amplitude", "centre", "width", "initial planes"],
                        "parallelism": "single GPU", "l2": L2_NOTE},
             "forward_updates_per_s": inner / fwd, "adjoint_updates_per_s": inner / bwd,
+            "roofline_adjoint": fp64_roof("lw_adjoint_kernel<double>", ADJ_FLOP_PER_UPDATE,
+                                          ADJ_INSTR_PER_UPDATE, bwd),
             "grad": [float(x) for x in grads],
-            "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clk,
+            "roofline": fp64_roof("lw_step_kernel<double>", FP64_FLOP_PER_UPDATE,
+                                  FP64_INSTR_PER_UPDATE, fwd),
+            "cpu_baseline": None, "e2e": None, "clocks": clk,
             "gpu_launches": args.steps * 2 * (n_outer * w.substeps),
         }
         print(json.dumps(line))
@@ -459,6 +485,8 @@ def main() -> int:
     ap.add_argument("--substeps", type=int, default=None,
                     help="Lax-Wendroff steps per outer step (default: the workload's; 0: from "
                          "the stability bound)")
+    ap.add_argument("--instances", type=int, default=0,
+                    help="batched workload: the first N of its 24 instances (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
