@@ -242,12 +242,18 @@ lw_step2_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__re
 // column and the load latency of column p + 1 overlaps the arithmetic of
 // column p.  The arithmetic is that of lw_step2_kernel.
 constexpr int kRingSlots = 3;
-constexpr int kSlotCols = 4 + kNCH + kNCN;   // state, half-node table, node table
+// The state column either goes through the ring with the tables (more
+// shared memory per warp, fewer warps per SM) or is loaded into registers
+// one column ahead (less shared memory, more warps).
+constexpr bool kRingStagesState = false;
+constexpr int kSlotCols = (kRingStagesState ? 4 : 0) + kNCH + kNCN;
+constexpr int kSlotHalf = kRingStagesState ? 4 : 0;          // offset of the half-node table
+constexpr int kSlotNode = kSlotHalf + kNCH;                   // offset of the node table
 
 template <typename T, int K>
 constexpr int ring_warps()
 {
-    return K == 1 ? 20 : K == 2 ? 8 : 4;
+    return kRingStagesState ? (K == 1 ? 20 : K == 2 ? 8 : 4) : (K == 1 ? 24 : K == 2 ? 12 : 4);
 }
 
 template <typename T, int K>
@@ -279,17 +285,17 @@ __device__ __forceinline__ void ring_fetch(T *slot, const T *__restrict__ u, con
                                            const T *__restrict__ node, int p, int Nr, int row)
 {
     constexpr int NP = 32 * K, B = K * (int)sizeof(T);
-    if (p >= 0 && p < Nr) {
+    if (kRingStagesState && p >= 0 && p < Nr) {
 #pragma unroll
         for (int c = 0; c < 4; ++c) cp_async<B>(slot + c * NP + row, u + ((size_t)p * 4 + c) * NP + row);
     }
     if (p >= 1 && p < Nr) {
 #pragma unroll
         for (int q = 0; q < kNCH; ++q)
-            cp_async<B>(slot + (4 + q) * NP + row, half + ((size_t)(p - 1) * kNCH + q) * NP + row);
+            cp_async<B>(slot + (kSlotHalf + q) * NP + row, half + ((size_t)(p - 1) * kNCH + q) * NP + row);
 #pragma unroll
         for (int q = 0; q < kNCN; ++q)
-            cp_async<B>(slot + (4 + kNCH + q) * NP + row, node + ((size_t)(p - 1) * kNCN + q) * NP + row);
+            cp_async<B>(slot + (kSlotNode + q) * NP + row, node + ((size_t)(p - 1) * kNCN + q) * NP + row);
     }
     cp_async_commit();
 }
@@ -316,6 +322,11 @@ lw_step2_ring_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T 
         zero_col<T, K>(u1m);
         zero_col<T, K>(h2m);
         ring_fetch<T, K>(ring, u_in, half, node, i0 - 2, Nr, row);
+        T cn[4][K];   // the state column p + 1, loaded one column ahead (unstaged state)
+        if (!kRingStagesState) {
+            if (i0 - 2 >= 0) load_col<T, K>(u_in + (size_t)(i0 - 2) * SP + row, cn);
+            else zero_col<T, K>(cn);
+        }
         int cur = 0;
         for (int p = i0 - 2; p <= i1 + 1; ++p) {
             const int nxt = cur == kRingSlots - 1 ? 0 : cur + 1;
@@ -328,28 +339,39 @@ lw_step2_ring_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T 
             const T *sc = ring + cur * kSlotCols * NP;    // column p: u_p, half_{p-1}, node_{p-1}
             const T *sp = ring + prv * kSlotCols * NP;    // column p - 1: half_{p-2}, node_{p-2}
             T c0[4][K], h1p[4][K], u1c[4][K], h2p[4][K];
-            if (p >= 0 && p < Nr) load_col<T, K>(sc + row, c0);
-            else zero_col<T, K>(c0);
+            if (kRingStagesState) {
+                if (p >= 0 && p < Nr) load_col<T, K>(sc + row, c0);
+                else zero_col<T, K>(c0);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int t = 0; t < K; ++t) c0[c][t] = cn[c][t];
+                if (p + 1 >= 0 && p + 1 < Nr && p + 1 <= i1 + 1)
+                    load_col<T, K>(u_in + (size_t)(p + 1) * SP + row, cn);
+                else
+                    zero_col<T, K>(cn);
+            }
             if (p >= i0 - 1 && p >= 1 && p < Nr)
-                half_node<T, K>(a0, c0, sc + 4 * NP + row, eh, h1p);
+                half_node<T, K>(a0, c0, sc + kSlotHalf * NP + row, eh, h1p);
             else
                 zero_col<T, K>(h1p);
             const int q = p - 1;
             if (p >= i0 && q >= 1 && q <= Nr - 2)
-                full_node<T, K>(h1m, h1p, a0, sc + (4 + kNCH) * NP + row, en, u1c);
+                full_node<T, K>(h1m, h1p, a0, sc + kSlotNode * NP + row, en, u1c);
             else
                 zero_col<T, K>(u1c);
             if ((obs_mask & 1) && q >= i0 && q < i1)
                 observe<T, K>(q, lane, u1c, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, 0);
             const int r = p - 2;
             if (p >= i0 + 1 && r >= 0 && r + 1 < Nr)
-                half_node<T, K>(u1m, u1c, sp + 4 * NP + row, eh, h2p);
+                half_node<T, K>(u1m, u1c, sp + kSlotHalf * NP + row, eh, h2p);
             else
                 zero_col<T, K>(h2p);
             if (p >= i0 + 2) {
                 T o[4][K];
                 if (r >= 1 && r <= Nr - 2)
-                    full_node<T, K>(h2m, h2p, u1m, sp + (4 + kNCH) * NP + row, en, o);
+                    full_node<T, K>(h2m, h2p, u1m, sp + kSlotNode * NP + row, en, o);
                 else
                     zero_col<T, K>(o);
                 store_col<T, K>(u_out + (size_t)r * SP + row, o);
