@@ -439,6 +439,19 @@ def run_adjoint(args, tk, torch, rank, world, local):
                 "launch_us": launch_s * 1e6,
                 "peak_source": "152 SMs x 2 DFMA/clk (measured) x 2 flop x median SM clock "
                                f"{f_clk / 1e6:.0f} MHz"}
+    pgrad = None
+    if args.param_gradient:
+        # dL/da and dL/dM of the same loss at the workload's parameters
+        with torch.no_grad():
+            W = tk.waveforms(g, *planes(*(torch.tensor(v, dtype=torch.float64, device="cuda")
+                                          for v in (w.amp, w.center, w.width))), n_outer)
+            dW = (2.0 * (W - target)).cpu().numpy()           # [obs][samples][2]
+        pgrad = {"checkpoint_every_outer_steps": args.checkpoint_every}
+        for name in ("a", "M"):
+            torch.cuda.synchronize()
+            t0p = time.perf_counter()
+            pgrad["dL_d" + name] = g.param_gradient(name, dW, args.checkpoint_every)
+            pgrad["seconds_" + name] = time.perf_counter() - t0p
     if rank == 0:
         line = {
             "metric": "grid-point updates/s (forward + adjoint)", "value": value, "unit": "updates/s",
@@ -453,7 +466,7 @@ def run_adjoint(args, tk, torch, rank, world, local):
             "forward_updates_per_s": inner / fwd, "adjoint_updates_per_s": inner / bwd,
             "roofline_adjoint": fp64_roof("lw_adjoint_kernel<double>", ADJ_FLOP_PER_UPDATE,
                                           ADJ_INSTR_PER_UPDATE, bwd),
-            "grad": [float(x) for x in grads],
+            "grad": [float(x) for x in grads], "param_gradient": pgrad,
             "roofline": fp64_roof("lw_step_kernel<double>", FP64_FLOP_PER_UPDATE,
                                   FP64_INSTR_PER_UPDATE, fwd),
             "cpu_baseline": None, "e2e": None, "clocks": clk,
@@ -485,6 +498,11 @@ def main() -> int:
     ap.add_argument("--substeps", type=int, default=None,
                     help="Lax-Wendroff steps per outer step (default: the workload's; 0: from "
                          "the stability bound)")
+    ap.add_argument("--param-gradient", action="store_true",
+                    help="adjoint workload: also dL/da and dL/dM through checkpointed "
+                         "recomputation (after the timed region)")
+    ap.add_argument("--checkpoint-every", type=int, default=150,
+                    help="outer steps between checkpoints for --param-gradient")
     ap.add_argument("--instances", type=int, default=0,
                     help="batched workload: the first N of its 24 instances (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -187,6 +187,27 @@ tk_status tk_extract_noalloc(tk_solver *S, int obs_id, int first, int count, dou
 tk_status tk_adjoint(tk_solver *S, const double *dL_dwave, const double *dL_dfinal, int on_device,
                      double *grad, int grad_on_device, int independent_pi);
 
+/* Gradient of a waveform loss with respect to a black-hole parameter of the
+ * coefficients (Eq. 1): param 0 the spin a, param 1 the mass M, for the
+ * trajectory taken since tk_set_initial_data (FP64 solvers; TK_ERR_STATE if
+ * the state was replaced by tk_set_state since).  dL_dwave as for tk_adjoint:
+ * [obs][samples][2] = dL/dRe W, dL/dIm W for every sample taken.  The
+ * gradient is the exact one of the discrete scheme up to the derivative of
+ * the coefficient tables, which is a 4-point central difference in the
+ * parameter (step 1e-3 M, or a quarter of M - |a| if smaller): of relative
+ * accuracy ~1e-10.  It includes the momentum's dependence on the parameter
+ * when Pi^0 was derived from Phi^0 (NULL pi planes).
+ * The adjoint state at inner step j needs u^j, so the trajectory is
+ * recomputed: checkpoints of the state every checkpoint_every outer steps
+ * (<= 0: about sqrt(samples / substeps), the choice that minimises memory),
+ * then, segment by segment from the last, the segment's inner states from its
+ * checkpoint, against which the adjoint sweep runs.  Device memory:
+ * (samples / C + C * substeps) states plus three table-sized arrays; the cost
+ * is about two forward runs plus one adjoint run plus the tangent
+ * contractions.  Writes the gradient to *grad (host).  Synchronizes. */
+tk_status tk_param_gradient(tk_solver *S, int param, const double *dL_dwave, int on_device,
+                            int checkpoint_every, double *grad);
+
 /* Current state as planes4 (4 * Ntheta * Nr doubles), host or device. */
 tk_status tk_get_state(tk_solver *S, double *planes4, int on_device);
 

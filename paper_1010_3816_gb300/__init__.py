@@ -32,7 +32,7 @@ EXPORTS = ("tk_make_grid", "tk_precompute_coeffs", "tk_set_initial_data", "tk_ad
            "tk_batch_create", "tk_batch_step", "tk_batch_tune", "tk_batch_set_segment",
            "tk_batch_set_graph_chunk", "tk_batch_info", "tk_batch_last_error", "tk_batch_destroy",
            "tk_extract_noalloc", "tk_adjoint", "tk_set_initial_gaussian", "tk_get_substeps",
-           "tk_set_steps_per_launch")
+           "tk_set_steps_per_launch", "tk_param_gradient")
 
 
 class TkError(RuntimeError):
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH):
                                                   C.c_double, C.c_uint64]),
             "tk_get_substeps": (C.c_int, [_vp, _ip]),
             "tk_set_steps_per_launch": (C.c_int, [_vp, C.c_int]),
+            "tk_param_gradient": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_int,
+                                            C.POINTER(C.c_double)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -233,6 +235,16 @@ def tk_adjoint(h, grad, dL_dwave=None, dL_dfinal=None, independent_pi: bool = Fa
     _check(h, load_library().tk_adjoint(h, pw, pf, locs.pop(), pg, dg, 1 if independent_pi else 0))
     if dg == 0 and isinstance(grad, np.ndarray) and kg is not grad:
         grad[...] = kg
+
+
+def tk_param_gradient(h, param: int, dL_dwave, checkpoint_every: int = 0) -> float:
+    """dL/da (param 0) or dL/dM (param 1) for the waveform-loss gradient dL_dwave
+    [obs][samples][2] (numpy or CUDA tensor), by checkpointed recomputation."""
+    p, dev, _keep = _arg(dL_dwave)
+    g = C.c_double(0.0)
+    _check(h, load_library().tk_param_gradient(h, int(param), p, dev, int(checkpoint_every),
+                                               C.byref(g)))
+    return g.value
 
 
 def tk_steps_done(h) -> int:
@@ -390,6 +402,11 @@ class Solver:
 
     def steps_done(self) -> int:
         return tk_steps_done(self.h)
+
+    def param_gradient(self, param, dL_dwave, checkpoint_every=0) -> float:
+        """param: "a" or "M" (or 0, 1)."""
+        idx = {"a": 0, "M": 1}.get(param, param)
+        return tk_param_gradient(self.h, idx, dL_dwave, checkpoint_every)
 
     def check_finite(self):
         tk_check_finite(self.h)

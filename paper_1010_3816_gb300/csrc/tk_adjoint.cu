@@ -18,6 +18,11 @@
 // A warp owns all theta rows of a range of output columns and walks it left
 // to right; the work split and the hand-off of the left-edge eta between the
 // warps of a block are those of the forward step kernel.
+#include <math.h>
+#include <string.h>
+
+#include <vector>
+
 #include "tk_solver_impl.h"
 #include "tk_stencil.cuh"
 
@@ -345,6 +350,147 @@ __global__ void initial_transpose_kernel(int Nr, int Nth, int NP, double drs,
     for (int c = 0; c < nout; ++c) out[c * plane + k] = g[c];
 }
 
+// ---- gradients with respect to the black-hole parameters (a or M) ----
+//
+// With the tables T(p) of one inner step u^{j+1} = A(p) u^j, the loss
+// gradient is dL/dp = sum_j lam~^{j+1} . (dA/dp) u^j (+ the initial-data
+// term below), lam~^{j+1} the adjoint state the adjoint kernel loads (with
+// the waveform gradient of the step added and the radial edges zeroed).  By
+// the product rule through the half nodes h = H u,
+//   (dA/dp) u at node i = N'(h_{i-1/2}, h_{i+1/2}) + N(h'_{i-1/2}, h'_{i+1/2}),
+// where N' is the node update with the derivative tables and no constant
+// terms, h' = H' u the half nodes with the derivative tables, and N applies
+// the ordinary node tables to h'.  One warp per column range, recomputing
+// its left edge; every block adds its partial sum to its own slot of acc, so
+// the sum is in a fixed order.
+template <int K>
+__global__ void __launch_bounds__(128)
+param_tangent_kernel(const double *__restrict__ u, const double *__restrict__ lam,
+                     const double *__restrict__ half, const double *__restrict__ node,
+                     const double *__restrict__ dhalf, const double *__restrict__ dnode, int Nr,
+                     double eh, double en, const InjectArgs inj, double *__restrict__ acc)
+{
+    constexpr int NP = 32 * K;
+    constexpr size_t SP = 4 * NP, HP = (size_t)kNCH * NP, NQ = (size_t)kNCN * NP;
+    __shared__ double part[4];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int i0, i1, left;
+    warp_range<4>(Nr, wib, &i0, &i1, &left);
+    const int row = lane * K;
+    double sum = 0.0;
+    if (i1 > i0) {
+        double ua[4][K], hm[4][K], dm[4][K], zero[4][K];
+        zero_col<double, K>(zero);
+        load_col<double, K>(u + (size_t)i0 * SP + row, ua);
+        if (i0 > 0) {
+            double ul[4][K];
+            load_col<double, K>(u + (size_t)(i0 - 1) * SP + row, ul);
+            half_node<double, K>(ul, ua, half + (size_t)(i0 - 1) * HP + row, eh, hm);
+            half_node<double, K>(ul, ua, dhalf + (size_t)(i0 - 1) * HP + row, 0.0, dm);
+        } else {
+            zero_col<double, K>(hm);
+            zero_col<double, K>(dm);
+        }
+        for (int i = i0; i < i1; ++i) {
+            double uc[4][K], hp[4][K], dp[4][K];
+            if (i + 1 < Nr) {
+                load_col<double, K>(u + (size_t)(i + 1) * SP + row, uc);
+                half_node<double, K>(ua, uc, half + (size_t)i * HP + row, eh, hp);
+                half_node<double, K>(ua, uc, dhalf + (size_t)i * HP + row, 0.0, dp);
+            } else {
+                zero_col<double, K>(uc);
+                zero_col<double, K>(hp);
+                zero_col<double, K>(dp);
+            }
+            if (i >= 1 && i <= Nr - 2) {
+                double d1[4][K], d2[4][K], l[4][K];
+                full_node<double, K>(hm, hp, zero, dnode + (size_t)i * NQ + row, 0.0, d1);
+                full_node<double, K>(dm, dp, zero, node + (size_t)i * NQ + row, en, d2);
+                load_lam<double, K>(lam, i, Nr, lane, inj, l);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int t = 0; t < K; ++t) sum = fma(l[c][t], d1[c][t] + d2[c][t], sum);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    ua[c][t] = uc[c][t];
+                    hm[c][t] = hp[c][t];
+                    dm[c][t] = dp[c][t];
+                }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (lane == 0) part[wib] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) acc[blockIdx.x] += (part[0] + part[1]) + (part[2] + part[3]);
+}
+
+// Initial-data term for a momentum derived from Phi^0: Pi^0 = b d_* Phi^0
+// depends on the parameter through b, d Pi^0 / dp = (db/dp / b) Pi^0.
+// lam0 = dL/du^0.  Partial sums per block into part[blockIdx] (fixed order).
+__global__ void param_initial_kernel(int Nr, int Nth, int NP, const double *__restrict__ u0,
+                                     const double *__restrict__ lam0, const double *__restrict__ b_node,
+                                     const double *__restrict__ db_node, double *__restrict__ part)
+{
+    __shared__ double ws[8];
+    double sum = 0.0;
+    const long long n = (long long)Nr * NP;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(k / NP), jp = (int)(k - (long long)i * NP);
+        if (jp >= Nth || i == 0 || i == Nr - 1) continue;
+        const double f = db_node[k] / b_node[k];
+        const size_t col = (size_t)i * 4 * NP + jp;
+        sum = fma(lam0[col + 2 * NP], f * u0[col + 2 * NP], sum);
+        sum = fma(lam0[col + 3 * NP], f * u0[col + 3 * NP], sum);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+    if (lane == 0) ws[w] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += ws[k];
+        part[blockIdx.x] = t;
+    }
+}
+
+// dst += w * src over n doubles.
+__global__ void axpy_kernel(size_t n, double w, const double *__restrict__ src, double *__restrict__ dst)
+{
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        dst[k] = fma(w, src[k], dst[k]);
+}
+
+cudaError_t launch_axpy(size_t n, double w, const double *src, double *dst, cudaStream_t st)
+{
+    size_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    axpy_kernel<<<(unsigned)blocks, 256, 0, st>>>(n, w, src, dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_param_tangent(int K, int blocks, const double *u, const double *lam,
+                                 const double *half, const double *node, const double *dhalf,
+                                 const double *dnode, int Nr, double dt_in, const InjectArgs &inj,
+                                 double *acc, cudaStream_t st)
+{
+    const double eh = 0.25 * dt_in, en = 0.5 * dt_in;
+    if (K == 1)
+        param_tangent_kernel<1><<<blocks, 128, 0, st>>>(u, lam, half, node, dhalf, dnode, Nr, eh, en, inj, acc);
+    else if (K == 2)
+        param_tangent_kernel<2><<<blocks, 128, 0, st>>>(u, lam, half, node, dhalf, dnode, Nr, eh, en, inj, acc);
+    else
+        param_tangent_kernel<4><<<blocks, 128, 0, st>>>(u, lam, half, node, dhalf, dnode, Nr, eh, en, inj, acc);
+    return cudaGetLastError();
+}
+
 template <typename T, int K, int W>
 constexpr size_t adj_smem_bytes()
 {
@@ -549,5 +695,186 @@ extern "C" tk_status tk_adjoint(tk_solver *S, const double *dL_dwave, const doub
     if (e == cudaSuccess && (!grad_on_device || !on_device)) e = cudaStreamSynchronize(S->stream);
     cleanup();
     if (e != cudaSuccess) return tkh::fail(S, TK_ERR_CUDA, "tk_adjoint: %s", cudaGetErrorString(e));
+    return TK_OK;
+}
+
+// Gradient of a waveform loss with respect to the spin a (param 0) or the mass
+// M (param 1), through checkpointed recomputation of the trajectory.
+extern "C" tk_status tk_param_gradient(tk_solver *S, int param, const double *dL_dwave, int on_device,
+                                       int checkpoint_every, double *grad)
+{
+    tk_status st = tkh::enter(S);
+    if (st != TK_OK) return st;
+    if (!grad || !dL_dwave) return tkh::fail(S, TK_ERR_ARG, "tk_param_gradient: NULL argument");
+    if (param != 0 && param != 1) return tkh::fail(S, TK_ERR_ARG, "tk_param_gradient: param %d is not 0 (a) or 1 (M)", param);
+    if (S->precision != TK_PREC_F64)
+        return tkh::fail(S, TK_ERR_ARG, "tk_param_gradient: FP64 solvers only");
+    if (!S->have_state || !S->init_valid)
+        return tkh::fail(S, TK_ERR_STATE, "tk_param_gradient: needs a trajectory from tk_set_initial_data "
+                                          "(not restarted with tk_set_state)");
+    if (S->nobs == 0) return tkh::fail(S, TK_ERR_ARG, "tk_param_gradient: no observers");
+    const long long count = S->count;
+    if (count <= 0) return tkh::fail(S, TK_ERR_STATE, "tk_param_gradient: no steps taken");
+    const int k = S->substeps;
+    long long C = checkpoint_every;
+    if (C <= 0) {
+        C = (long long)sqrt((double)count / k);
+        if (C < 1) C = 1;
+    }
+    if (C > count) C = count;
+    const long long nck = (count + C - 1) / C;
+    const size_t se = (size_t)S->Nr * 4 * S->NP, sb = se * sizeof(double);
+    const size_t nh = (size_t)S->Nr * tk::kNCH * S->NP, nn = (size_t)S->Nr * tk::kNCN * S->NP;
+    const size_t nb = (size_t)S->Nr * S->NP;
+
+    // scratch, freed on every exit
+    double *dwave = nullptr, *thalf = nullptr, *tnode = nullptr, *tb = nullptr, *tw = nullptr;
+    double *tx = nullptr, *tang = nullptr, *ck = nullptr, *seg = nullptr, *acc = nullptr;
+    auto cleanup = [&]() {
+        void *p[] = {thalf, tnode, tb, tw, tx, tang, ck, seg, acc};
+        for (void *q : p)
+            if (q) cudaFree(q);
+        if (dwave && !on_device) cudaFree(dwave);
+    };
+    auto bail = [&](tk_status s2) {
+        cleanup();
+        return s2;
+    };
+    for (int q = 0; q < 2; ++q)
+        if (!S->adj[q] && (st = tkh::alloc(S, &S->adj[q], sb)) != TK_OK) return bail(st);
+    if (!S->dhalf && (st = tkh::alloc(S, (void **)&S->dhalf, nh * sizeof(double))) != TK_OK) return bail(st);
+    if (!S->dnode && (st = tkh::alloc(S, (void **)&S->dnode, nn * sizeof(double))) != TK_OK) return bail(st);
+    if (!S->db_node && (st = tkh::alloc(S, (void **)&S->db_node, nb * sizeof(double))) != TK_OK) return bail(st);
+    if ((st = tkh::alloc(S, (void **)&thalf, nh * sizeof(double))) != TK_OK ||
+        (st = tkh::alloc(S, (void **)&tnode, nn * sizeof(double))) != TK_OK ||
+        (st = tkh::alloc(S, (void **)&tb, nb * sizeof(double))) != TK_OK ||
+        (st = tkh::alloc(S, (void **)&tw, (size_t)S->NP * sizeof(double))) != TK_OK ||
+        (st = tkh::alloc(S, (void **)&tx, (size_t)2 * S->Nr * sizeof(double))) != TK_OK ||
+        (st = tkh::alloc(S, (void **)&tang, (size_t)2 * S->NP * sizeof(double))) != TK_OK)
+        return bail(st);
+    if (on_device) {
+        dwave = const_cast<double *>(dL_dwave);
+    } else {
+        if ((st = tkh::alloc(S, (void **)&dwave, (size_t)S->nobs * count * 2 * sizeof(double))) != TK_OK)
+            return bail(st);
+        cudaError_t e = cudaMemcpyAsync(dwave, dL_dwave, (size_t)S->nobs * count * 2 * sizeof(double),
+                                        cudaMemcpyHostToDevice, S->stream);
+        if (e != cudaSuccess) return bail(tkh::fail(S, TK_ERR_CUDA, "tk_param_gradient: %s", cudaGetErrorString(e)));
+    }
+    cudaError_t e = cudaSuccess;
+    const double dt_in = S->dt / k;
+    // 1. derivative tables, 4-point central differences in the parameter:
+    //    dT/dp = [8 (T(p+d) - T(p-d)) - (T(p+2d) - T(p-2d))] / (12 d)
+    {
+        const double M = S->kerr.M, a = S->kerr.a;
+        double d = 1e-3 * M;
+        if (d > 0.25 * (M - fabs(a))) d = 0.25 * (M - fabs(a));
+        const double off[4] = {d, -d, 2 * d, -2 * d};
+        const double wgt[4] = {8.0 / (12 * d), -8.0 / (12 * d), -1.0 / (12 * d), 1.0 / (12 * d)};
+        e = cudaMemsetAsync(S->dhalf, 0, nh * sizeof(double), S->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(S->dnode, 0, nn * sizeof(double), S->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(S->db_node, 0, nb * sizeof(double), S->stream);
+        for (int q = 0; q < 4 && e == cudaSuccess; ++q) {
+            tk::Kerr P = S->kerr;
+            if (param == 0) P.a += off[q];
+            else P.M += off[q];
+            e = tk::launch_invert_tortoise(P, S->rs_min, S->drs, S->Nr, tx, tx + S->Nr, S->stream);
+            if (e == cudaSuccess)
+                e = tk::launch_coeff_tables(P, S->variable, S->Nr, S->Nth, S->NP, S->drs, dt_in, tx,
+                                            tx + S->Nr, tang, 0, thalf, tnode, tb, tw, S->stream);
+            if (e == cudaSuccess) e = tk::launch_axpy(nh, wgt[q], thalf, S->dhalf, S->stream);
+            if (e == cudaSuccess) e = tk::launch_axpy(nn, wgt[q], tnode, S->dnode, S->stream);
+            if (e == cudaSuccess) e = tk::launch_axpy(nb, wgt[q], tb, S->db_node, S->stream);
+        }
+    }
+    if (e != cudaSuccess) return bail(tkh::fail(S, TK_ERR_CUDA, "tk_param_gradient: %s", cudaGetErrorString(e)));
+    // 2. checkpoints of the trajectory every C outer steps, from u^0
+    if ((st = tkh::alloc(S, (void **)&ck, (size_t)nck * sb)) != TK_OK) return bail(st);
+    if ((st = tkh::alloc(S, (void **)&seg, (size_t)(C * k) * sb)) != TK_OK) return bail(st);
+    tk::StepLaunch L;
+    tkh::fill_launch(S, L);
+    L.write_wave = 0;
+    e = cudaMemcpyAsync(ck, S->u_init, sb, cudaMemcpyDeviceToDevice, S->stream);
+    for (long long c = 0; c + 1 < nck && e == cudaSuccess; ++c) {
+        const double *src = ck + (size_t)c * se;
+        double *dst = ck + (size_t)(c + 1) * se;
+        // C outer steps: ping-pong through the first two segment slots
+        const void *in = src;
+        for (long long j = 0; j < C * k && e == cudaSuccess; ++j) {
+            void *out = (j == C * k - 1) ? (void *)dst : (void *)(seg + (size_t)(j & 1) * se);
+            L.u_in = in;
+            L.u_out = out;
+            e = tk::launch_lw_step(L, S->stream);
+            in = out;
+        }
+    }
+    // 3. backward over the segments: recompute the segment's inner states,
+    //    then the tangent contraction and the adjoint step for each of them
+    int blocks = 0;
+    if (e == cudaSuccess) {
+        const int K = S->K;
+        int per = 0;
+        if (K == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tk::param_tangent_kernel<1>, 128, 0);
+        else if (K == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tk::param_tangent_kernel<2>, 128, 0);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tk::param_tangent_kernel<4>, 128, 0);
+        if (per < 1) per = 1;
+        blocks = S->num_sms * per;
+        if (blocks > S->Nr / 4) blocks = S->Nr / 4;
+        if (blocks < 1) blocks = 1;
+    }
+    const int pblocks = 1024;
+    if (e == cudaSuccess && (st = tkh::alloc(S, (void **)&acc, (size_t)(blocks + pblocks) * sizeof(double))) != TK_OK)
+        return bail(st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, (size_t)(blocks + pblocks) * sizeof(double), S->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S->adj[0], 0, sb, S->stream);
+    tk::InjectArgs inj;
+    memset(&inj, 0, sizeof inj);
+    inj.count = count;
+    inj.dwave = dwave;
+    inj.w_row = S->w_row;
+    inj.obs = L.obs;
+    int cur = 0;
+    for (long long c = nck - 1; c >= 0 && e == cudaSuccess; --c) {
+        const long long t0 = c * C, len = (c == nck - 1) ? count - t0 : C;
+        // seg[j] = u^{t0 k + j}, j < len k
+        e = cudaMemcpyAsync(seg, ck + (size_t)c * se, sb, cudaMemcpyDeviceToDevice, S->stream);
+        for (long long j = 0; j + 1 < len * k && e == cudaSuccess; ++j) {
+            L.u_in = seg + (size_t)j * se;
+            L.u_out = seg + (size_t)(j + 1) * se;
+            e = tk::launch_lw_step(L, S->stream);
+        }
+        for (long long t = t0 + len - 1; t >= t0 && e == cudaSuccess; --t)
+            for (int kk = 0; kk < k && e == cudaSuccess; ++kk) {
+                inj.on = (kk == 0);
+                inj.sample = t;
+                const long long j = (t - t0) * k + (k - 1 - kk);     // u^j is the step's input
+                e = tk::launch_param_tangent(S->K, blocks, seg + (size_t)j * se, (const double *)S->adj[cur],
+                                             (const double *)S->half, (const double *)S->node, S->dhalf,
+                                             S->dnode, S->Nr, dt_in, inj, acc, S->stream);
+                if (e == cudaSuccess)
+                    e = tk::launch_adjoint_step(0, S->K, S->adj[cur], S->adj[cur ^ 1], S->half, S->node,
+                                                S->Nr, S->adj_blocks, S->adj_warps, dt_in, inj, S->stream);
+                cur ^= 1;
+            }
+    }
+    // 4. the initial-data term (momentum derived from Phi^0 through b)
+    if (e == cudaSuccess && S->init_pi_derived) {
+        tk::param_initial_kernel<<<pblocks, 256, 0, S->stream>>>(S->Nr, S->Nth, S->NP,
+                                                                  (const double *)S->u_init,
+                                                                  (const double *)S->adj[cur], S->b_node,
+                                                                  S->db_node, acc + blocks);
+        e = cudaGetLastError();
+    }
+    std::vector<double> h((size_t)blocks + pblocks, 0.0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), acc, h.size() * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    if (e != cudaSuccess)
+        return bail(tkh::fail(S, e == cudaErrorMemoryAllocation ? TK_ERR_OOM : TK_ERR_CUDA,
+                              "tk_param_gradient: %s", cudaGetErrorString(e)));
+    double g = 0.0;
+    for (size_t q = 0; q < h.size(); ++q) g += h[q];
+    *grad = g;
+    cleanup();
     return TK_OK;
 }

@@ -46,7 +46,7 @@ void release(tk_solver *S)
 {
     void *ptrs[] = {S->u[0], S->u[1], S->half, S->node, S->b_node, S->w_row,
                     S->x_node, S->x_half, S->ang, S->staging, S->flag, S->stiff, S->ctr, S->wave,
-                    S->adj[0], S->adj[1]};
+                    S->adj[0], S->adj[1], S->u_init, S->dhalf, S->dnode, S->db_node};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < 2; ++k)
@@ -306,6 +306,18 @@ tk_status tk_set_initial_data(tk_solver *S, const double *phi_re, const double *
     st = import_planes(S, phi_re, phi_im, pi_re, pi_im, on_device);
     if (st != TK_OK) return st;
     TK_CUDA(S, cudaMemsetAsync(S->ctr, 0, 2 * sizeof(long long), S->stream));
+    // keep u^0 (FP64) for the parameter gradients, which recompute the trajectory
+    S->init_valid = false;
+    if (S->precision == TK_PREC_F64) {
+        const size_t bytes = state_elems(S) * S->esz;
+        if (!S->u_init) {
+            st = alloc(S, &S->u_init, bytes);
+            if (st != TK_OK) return st;
+        }
+        TK_CUDA(S, cudaMemcpyAsync(S->u_init, S->u[S->cur], bytes, cudaMemcpyDeviceToDevice, S->stream));
+        S->init_valid = true;
+        S->init_pi_derived = (pi_re == nullptr);
+    }
     S->have_state = true;
     S->count = 0;
     S->steps_done = 0;
@@ -556,6 +568,7 @@ tk_status tk_set_state(tk_solver *S, const double *planes4, int on_device)
     if (!S->have_state) return fail(S, TK_ERR_STATE, "tk_set_state before tk_set_initial_data");
     if (!planes4) return fail(S, TK_ERR_ARG, "tk_set_state: planes4 is NULL");
     const size_t plane = (size_t)S->Nth * S->Nr;
+    S->init_valid = false;   // the trajectory no longer starts from the stored u^0
     return import_planes(S, planes4, planes4 + plane, planes4 + 2 * plane, planes4 + 3 * plane, on_device);
 }
 

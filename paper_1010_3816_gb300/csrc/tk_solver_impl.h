@@ -26,6 +26,11 @@ struct tk_solver {
     unsigned long long *stiff = nullptr;  // [max omega^2, max b] as double bit patterns
     long long *ctr = nullptr;   // [0]: sample index of the next outer step, [1]: blocks done
     void *adj[2] = {nullptr, nullptr};  // adjoint state levels (tk_adjoint), allocated on use
+    // parameter gradients (tk_param_gradient): u^0 and the derivative tables
+    void *u_init = nullptr;             // copy of u^0 (FP64 solvers)
+    bool init_valid = false;            // u_init starts the current trajectory
+    bool init_pi_derived = false;       // Pi^0 = b d_* Phi^0 (depends on the parameters through b)
+    double *dhalf = nullptr, *dnode = nullptr, *db_node = nullptr;   // d(tables)/d(parameter)
     // physics
     tk::Kerr kerr{};
     bool have_coeffs = false, have_state = false;
