@@ -65,7 +65,7 @@ FP32_FMA_PER_CLK_PER_SM = 128
 MEASURED_TRAFFIC = {
     ("kerr_a0.9_25601x64_38400steps", 0): (333.902592e6 + 38.241280e6,
                                            "profiles/lw_step_f64_kerr_25601x64.md"),
-    ("kerr_a0.9_25601x64_38400steps", 1): (194.818304e6 + 15.622144e6,
+    ("kerr_a0.9_25601x64_38400steps", 1): (210.219776e6 + 14.248960e6,
                                            "profiles/lw_step2_ring_f32_kerr_25601x64.md"),
 }
 L2_FLUSH_BYTES = 256 << 20          # twice the 129 MB L2
