@@ -230,13 +230,19 @@ tk_status tk_set_state(tk_solver *S, const double *planes4, int on_device);
 tk_status tk_stability_bound(tk_solver *S, double growth_per_step, double *dt_max,
                              int *substeps_needed);
 
-/* Lax-Wendroff steps per kernel launch: 1, 2, or 0 for the default (2 for
- * TK_PREC_F32, whose step is bound by memory traffic, 1 for TK_PREC_F64,
- * whose step is bound by FP64 arithmetic).  With 2, pairs of inner steps run
- * in one launch that reads the state and the coefficient tables once; each
- * warp recomputes the intermediate level one column beyond its range, which
- * adds arithmetic but no DRAM traffic.  Results are bit-identical either way.
- * Returns TK_ERR_ARG for other values. */
+/* Lax-Wendroff steps per kernel launch: 1, 2, -1 (every inner step of a
+ * tk_step call in one persistent launch), or 0 for the default: 2 for
+ * TK_PREC_F32, whose step is bound by memory traffic; for TK_PREC_F64, whose
+ * step is bound by FP64 arithmetic, 1, or -1 on grids too small for one block
+ * per SM (where launch overhead and latency dominate).  With 2,
+ * pairs of inner steps run in one launch that reads the state and the
+ * coefficient tables once; each warp recomputes the intermediate level one
+ * column beyond its range, which adds arithmetic but no DRAM traffic.  With
+ * -1, all blocks stay resident (cooperative launch) and each waits after
+ * every step for its two neighbouring blocks; the waits are bounded, and
+ * tk_step then synchronizes the stream and returns TK_ERR_INTERNAL if one
+ * ran out.  Results are bit-identical in every mode.  Returns TK_ERR_ARG for
+ * other values, and for -1 on a grid that fills the GPU. */
 tk_status tk_set_steps_per_launch(tk_solver *S, int steps);
 
 /* Lax-Wendroff steps per outer step in use (the count chosen at the last

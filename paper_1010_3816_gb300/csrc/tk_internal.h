@@ -16,6 +16,7 @@ namespace tk {
 
 constexpr int kMaxObservers = 16;
 constexpr int kMaxK = 4;          // theta rows per lane: Ntheta <= 32 * kMaxK
+constexpr int kNarrowWarps = 4;   // warps per block of a narrow launch (small grids)
 constexpr int kNCH = 11;          // half-node table entries
 constexpr int kNCN = 10;          // node table entries
 
@@ -111,6 +112,13 @@ cudaError_t launch_lw_step(const StepLaunch &L, cudaStream_t st);
 // Launch shape of the step kernel for a grid: returns the number of blocks
 // and sets *warps to the warps per block.
 int step_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
+// Many steps in one cooperative launch (small grids): the grid size for it,
+// 0 if it cannot run; the launch itself (L.u_in holds u^n, u_other is the
+// second level; flags: one zeroed unsigned int per block; *err set on a wait
+// that timed out).
+int persistent_grid_blocks(int precision, int K, int Nr, int num_sms);
+cudaError_t launch_lw_persistent(const StepLaunch &L, void *u_other, int n_inner, int substeps,
+                                 unsigned int *flags, int *err, cudaStream_t st);
 // Launch shape of the two-step kernel.
 int fused_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
 // Launch shape of the adjoint step kernel: returns the number of blocks and

@@ -49,6 +49,9 @@ struct tk_solver {
     bool auto_k = false;        // substeps from the stability bound at each precompute
     int blocks = 1;             // step kernel launch shape
     int warps = 4;
+    int persist = 0;            // 1: all inner steps of a tk_step call in one persistent launch
+    int persist_blocks = 0;     // its grid (0: the grid is too large for it)
+    unsigned int *pflags = nullptr;     // its per-block step flags, then the error flag
     int fuse = 0;               // 1: inner steps in pairs, one two-step launch per pair
     int fuse_mode = 0;          // as set by tk_set_steps_per_launch (0: automatic)
     int fused_blocks = 1;       // two-step kernel launch shape

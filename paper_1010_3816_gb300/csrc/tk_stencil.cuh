@@ -95,8 +95,6 @@ __device__ __forceinline__ void theta_neighbours(const T (&s)[K], T (&up)[K], T 
     }
 }
 
-constexpr int kNarrowWarps = 4;   // warps per block of a narrow launch
-
 // Work split.  Block b owns columns [b Nr / B, (b+1) Nr / B), within which
 // its warps take contiguous ranges, in warp order.  Warps w, w + 4, w + 8,
 // ... run on the same SM sub-partition, so the four quarters of the block's

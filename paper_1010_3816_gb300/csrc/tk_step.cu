@@ -61,16 +61,61 @@ constexpr int wide_warps()
     return sizeof(T) == 8 ? (K == 1 ? 24 : K == 2 ? 16 : 8) : (K == 1 ? 32 : K == 2 ? 24 : 16);
 }
 
-template <typename T, int K, int W>
-__global__ void __launch_bounds__(W * 32, wide_warps<T, K>() / W)
-lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__restrict__ half,
-               const T *__restrict__ node, int Nr, T eh, T en, const WaveArgs wa)
+// State loads of the one-step sweep: through L1 when the state is read-only
+// for the launch, from L2 (ld.global.cg) when other blocks of the same launch
+// have written it (the persistent kernel), so that no stale L1 line is read.
+template <typename T, int K, bool CG>
+__device__ __forceinline__ void load_state(const T *p, T (&u)[4][K])
+{
+    if constexpr (!CG) {
+        load_col<T, K>(p, u);
+    } else {
+        constexpr int NP = 32 * K;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const T *q = p + c * NP;
+            if constexpr (sizeof(T) == 8 && K == 1) {
+                u[c][0] = __ldcg(q);
+            } else if constexpr (sizeof(T) == 8) {
+#pragma unroll
+                for (int t = 0; t < K; t += 2) {
+                    const double2 x = __ldcg(reinterpret_cast<const double2 *>(q + t));
+                    u[c][t] = x.x;
+                    u[c][t + 1] = x.y;
+                }
+            } else if constexpr (K == 1) {
+                u[c][0] = __ldcg(q);
+            } else if constexpr (K == 2) {
+                const float2 x = __ldcg(reinterpret_cast<const float2 *>(q));
+                u[c][0] = x.x;
+                u[c][1] = x.y;
+            } else {
+                const float4 x = __ldcg(reinterpret_cast<const float4 *>(q));
+                u[c][0] = x.x;
+                u[c][1] = x.y;
+                u[c][2] = x.z;
+                u[c][3] = x.w;
+            }
+        }
+    }
+}
+
+// One Lax-Wendroff step over the block's columns (the body of lw_step_kernel):
+// every warp walks its range, the first warp of the block recomputes its left
+// half node, the others receive it through shared memory after a block
+// barrier.  write: observe this step; sample_offset: samples after the
+// counter's value.
+template <typename T, int K, int W, bool CG>
+__device__ __forceinline__ void step_sweep(unsigned char *sh_raw, const T *__restrict__ u_in,
+                                           T *__restrict__ u_out,
+                                           const T *__restrict__ half, const T *__restrict__ node,
+                                           int Nr, T eh, T en, const WaveArgs &wa, int write,
+                                           int sample_offset)
 {
     constexpr int NP = 32 * K;
     constexpr size_t SP = 4 * NP, HP = (size_t)kNCH * NP, NQ = (size_t)kNCN * NP;
     // per warp: [0] its last half node (read by the right neighbour),
     //           [1] u^n at its first column, [2] u^{n+1/2} right of its first column
-    extern __shared__ __align__(16) unsigned char sh_raw[];
     T(*sh)[3][4][NP] = reinterpret_cast<T(*)[3][4][NP]>(sh_raw);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -81,10 +126,10 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
 
     T ua[4][K], hm[4][K];
     if (i1 > i0) {
-        load_col<T, K>(u_in + (size_t)i0 * SP + row, ua);
+        load_state<T, K, CG>(u_in + (size_t)i0 * SP + row, ua);
         if (lead && i0 > 0) {
             T ul[4][K];
-            load_col<T, K>(u_in + (size_t)(i0 - 1) * SP + row, ul);
+            load_state<T, K, CG>(u_in + (size_t)(i0 - 1) * SP + row, ul);
             half_node<T, K>(ul, ua, half + (size_t)(i0 - 1) * HP + row, eh, hm);
         } else {
             zero_col<T, K>(hm);
@@ -92,7 +137,7 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
         for (int i = i0; i < i1; ++i) {
             T uc[4][K], hp[4][K], o[4][K];
             if (i + 1 < Nr) {
-                load_col<T, K>(u_in + (size_t)(i + 1) * SP + row, uc);
+                load_state<T, K, CG>(u_in + (size_t)(i + 1) * SP + row, uc);
                 half_node<T, K>(ua, uc, half + (size_t)i * HP + row, eh, hp);
             } else {
                 zero_col<T, K>(uc);
@@ -110,7 +155,8 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
                 full_node<T, K>(hm, hp, ua, node + (size_t)i * NQ + row, en, o);
                 if (i == 0 || i == Nr - 1) zero_col<T, K>(o);
                 store_col<T, K>(u_out + (size_t)i * SP + row, o);
-                if (wa.write) observe<T, K>(i, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row);
+                if (write)
+                    observe<T, K>(i, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, sample_offset);
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c)
@@ -142,9 +188,82 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
         full_node<T, K>(hl, hp, ua, node + (size_t)i0 * NQ + row, en, o);
         if (i0 == 0 || i0 == Nr - 1) zero_col<T, K>(o);
         store_col<T, K>(u_out + (size_t)i0 * SP + row, o);
-        if (wa.write) observe<T, K>(i0, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row);
+        if (write) observe<T, K>(i0, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, sample_offset);
     }
+}
+
+template <typename T, int K, int W>
+__global__ void __launch_bounds__(W * 32, wide_warps<T, K>() / W)
+lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__restrict__ half,
+               const T *__restrict__ node, int Nr, T eh, T en, const WaveArgs wa)
+{
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    step_sweep<T, K, W, false>(sh_raw, u_in, u_out, half, node, Nr, eh, en, wa, wa.write, 0);
     if (wa.write) advance_sample(wa);
+}
+
+// Many Lax-Wendroff steps in one launch, for grids too small to fill the GPU
+// with long sweeps, where per-launch overhead would dominate.  All blocks are
+// resident at once (cooperative launch).  After each step a block publishes
+// the step count in flags[block] and waits until both neighbouring blocks
+// have published it: the next step reads one column of u from each of them,
+// and overwrites the level they read in this step.  Every wait is bounded:
+// after kMaxSpins polls the block sets *err and every block leaves its loop
+// (the state is then invalid and the host reports the error).  State loads go
+// through L2 (other blocks write them).  u0 holds u^n at the start; the result
+// is in u0 or u1 by the parity of n_inner.
+constexpr long long kMaxSpins = 1ll << 24;
+
+__device__ __forceinline__ unsigned int load_acquire(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool neighbour_barrier(unsigned int *flags, unsigned int epoch, int *err)
+{
+    __shared__ int ok;
+    __syncthreads();                       // the block's stores of this step are issued
+    if (threadIdx.x == 0) {
+        __threadfence();                   // and visible to the other blocks
+        atomicExch(&flags[blockIdx.x], epoch);
+        int good = 1;
+        for (int side = -1; side <= 1 && good; side += 2) {
+            const int nb = (int)blockIdx.x + side;
+            if (nb < 0 || nb >= (int)gridDim.x) continue;
+            long long spins = 0;
+            while (load_acquire(&flags[nb]) < epoch) {
+                if (++spins > kMaxSpins || *(volatile int *)err) {
+                    good = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (!good) atomicExch(err, 1);
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename T, int K, int W>
+__global__ void __launch_bounds__(W * 32, wide_warps<T, K>() / W)
+lw_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__restrict__ node, int Nr,
+                     T eh, T en, const WaveArgs wa, int n_inner, int substeps, unsigned int *flags,
+                     int *err)
+{
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    for (int s = 0; s < n_inner; ++s) {
+        const T *in = (s & 1) ? u1 : u0;
+        T *out = (s & 1) ? u0 : u1;
+        const int write = wa.write && ((s + 1) % substeps == 0);
+        step_sweep<T, K, W, true>(sh_raw, in, out, half, node, Nr, eh, en, wa, write,
+                                  (s + 1) / substeps - 1);
+        if (s + 1 < n_inner && !neighbour_barrier(flags, (unsigned)(s + 1), err)) break;
+    }
+    if (wa.write) advance_sample(wa, n_inner / substeps);
 }
 
 // Two Lax-Wendroff steps per launch, u^n -> u^{n+2}, for the HBM-bound
@@ -544,7 +663,72 @@ int fused_shape(int Nr, int num_sms, int *warps)
     return blocks < 1 ? 1 : blocks;
 }
 
+template <typename T, int K>
+int persistent_blocks(int Nr, int num_sms)
+{
+    constexpr int W = kNarrowWarps;
+    int n = 0;
+    if (step_smem_setup<T, K, W>() != cudaSuccess) return 0;
+    static cudaError_t e0 = cudaFuncSetAttribute(lw_persistent_kernel<T, K, W>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)step_smem_bytes<T, K, W>());
+    if (e0 != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_persistent_kernel<T, K, W>, W * 32,
+                                                      step_smem_bytes<T, K, W>()) != cudaSuccess ||
+        n < 1)
+        return 0;
+    int blocks = num_sms * n;
+    if (blocks > Nr / W) blocks = Nr / W;
+    return blocks < 1 ? 0 : blocks;
+}
+
+template <typename T, int K>
+cudaError_t launch_persistent_typed(const StepLaunch &L, void *u_other, int n_inner, int substeps,
+                                    unsigned int *flags, int *err, cudaStream_t st)
+{
+    constexpr int W = kNarrowWarps;
+    WaveArgs wa;
+    wa.write = L.write_wave;
+    wa.sample = L.sample_ctr;
+    wa.done = L.done_ctr;
+    wa.cap = L.wave_cap;
+    wa.wave = L.wave;
+    wa.w_row = L.w_row;
+    wa.obs = L.obs;
+    T *u0 = (T *)L.u_in, *u1 = (T *)u_other;
+    const T *half = (const T *)L.half, *node = (const T *)L.node;
+    int Nr = L.Nr;
+    T eh = (T)(0.25 * L.dt_inner), en = (T)(0.5 * L.dt_inner);
+    void *args[] = {&u0, &u1, &half, &node, &Nr, &eh, &en, &wa, &n_inner, &substeps, &flags, &err};
+    return cudaLaunchCooperativeKernel((const void *)lw_persistent_kernel<T, K, W>, dim3(L.blocks),
+                                       dim3(W * 32), args, step_smem_bytes<T, K, W>(), st);
+}
+
 }  // namespace
+
+int persistent_grid_blocks(int precision, int K, int Nr, int num_sms)
+{
+    if (precision == 0)
+        return K == 1 ? persistent_blocks<double, 1>(Nr, num_sms)
+             : K == 2 ? persistent_blocks<double, 2>(Nr, num_sms)
+                      : persistent_blocks<double, 4>(Nr, num_sms);
+    return K == 1 ? persistent_blocks<float, 1>(Nr, num_sms)
+         : K == 2 ? persistent_blocks<float, 2>(Nr, num_sms)
+                  : persistent_blocks<float, 4>(Nr, num_sms);
+}
+
+cudaError_t launch_lw_persistent(const StepLaunch &L, void *u_other, int n_inner, int substeps,
+                                 unsigned int *flags, int *err, cudaStream_t st)
+{
+    if (L.precision == 0) {
+        if (L.K == 1) return launch_persistent_typed<double, 1>(L, u_other, n_inner, substeps, flags, err, st);
+        if (L.K == 2) return launch_persistent_typed<double, 2>(L, u_other, n_inner, substeps, flags, err, st);
+        return launch_persistent_typed<double, 4>(L, u_other, n_inner, substeps, flags, err, st);
+    }
+    if (L.K == 1) return launch_persistent_typed<float, 1>(L, u_other, n_inner, substeps, flags, err, st);
+    if (L.K == 2) return launch_persistent_typed<float, 2>(L, u_other, n_inner, substeps, flags, err, st);
+    return launch_persistent_typed<float, 4>(L, u_other, n_inner, substeps, flags, err, st);
+}
 
 int fused_grid_shape(int precision, int K, int Nr, int num_sms, int *warps)
 {

@@ -1,4 +1,5 @@
-"""Two Lax-Wendroff steps per launch (tk_set_steps_per_launch).
+"""Launch structures of tk_step (tk_set_steps_per_launch): two Lax-Wendroff
+steps per launch, and every step of a call in one persistent launch.
 
 The two-step kernel does, per node and half node, the arithmetic of the
 one-step kernel on the same operands, so a solve with pairs of steps per
@@ -92,7 +93,42 @@ def test_steps_per_launch_argument():
     import paper_1010_3816_gb300 as tk
     w = _grid(401, 32)
     g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt)
-    for bad in (-1, 3):
+    for bad in (-2, 3):
         with pytest.raises(tk.TkError):
             g.set_steps_per_launch(bad)
+    g.close()
+
+
+PERSISTENT_CASES = [
+    (0, _grid(1601, 32, substeps=1), (17, 1, 40)),         # the 1601 x 32 workload's shape
+    (0, _grid(803, 64, substeps=2), (9, 11)),
+    (0, _grid(401, 128, substeps=3), (5,)),
+    (0, _grid(997, 40, substeps=1, variable=0, dt=0.01), (25,)),   # literal, padded rows
+    (1, _grid(1601, 32, substeps=2), (13, 8)),
+    (0, _grid(23, 8, substeps=1, observers=((-30.0, 1.5), (-29.0, 0.5))), (31,)),  # few columns
+]
+
+
+@pytest.mark.parametrize("precision,w,calls", PERSISTENT_CASES,
+                         ids=[f"case{k}" for k in range(len(PERSISTENT_CASES))])
+def test_persistent_launch_bit_identical(precision, w, calls):
+    """All inner steps of each tk_step call in one cooperative launch, blocks
+    waiting on their neighbours between steps: the same bits as one launch per
+    step, waveforms included."""
+    s1, w1 = _run(w, precision, 1, calls)
+    sp, wp = _run(w, precision, -1, calls)
+    assert np.isfinite(s1).all()
+    assert np.array_equal(s1, sp)
+    assert all(np.array_equal(a, b) for a, b in zip(w1, wp))
+    # and the automatic choice (persistent for FP64 on these small grids)
+    s0, w0 = _run(w, precision, 0, calls)
+    assert np.array_equal(s0, sp) and all(np.array_equal(a, b) for a, b in zip(w0, wp))
+
+
+def test_persistent_launch_refused_on_a_full_grid():
+    import paper_1010_3816_gb300 as tk
+    w = _grid(5003, 64)
+    g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt)
+    with pytest.raises(tk.TkError):
+        g.set_steps_per_launch(-1)
     g.close()

@@ -256,6 +256,7 @@ def test_graph_replay_matches_direct_launches():
                       substeps=w.substeps)
         g.precompute(w.a, w.M, w.s, w.m).set_initial(re, im)
         ids = [g.add_observer(r, t) for r, t in w.observers]
+        g.set_steps_per_launch(1)        # this grid would otherwise run as one persistent launch
         g.set_graph_chunk(chunk)
         g.step(100)
         g.step(3)
