@@ -451,6 +451,48 @@ class Batch:
         return tk_batch_info(self.b)
 
 
+def waveforms_with_params(solver: "Solver", a, M, s: int, m: int, phi_re, phi_im, n_steps: int):
+    """Like waveforms(), and also differentiable in the black-hole spin a and
+    mass M (0-dim float64 tensors): the forward pass runs the precompute at
+    (a, M, s, m), the initial data and the steps; the backward pass gives the
+    planes' gradient through tk_adjoint and dL/da, dL/dM through
+    tk_param_gradient (checkpointed recomputation of the trajectory), each
+    only when it is needed."""
+    import torch
+
+    class _WaveformsParams(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, a_, M_, pr, pi):
+            solver.precompute(float(a_), float(M_), s, m)
+            solver.set_initial(pr.detach().contiguous(), pi.detach().contiguous())
+            solver.step(n_steps)
+            out = []
+            for k in range(len(solver._observers)):
+                re = torch.empty(n_steps, dtype=torch.float64, device=pr.device)
+                im = torch.empty(n_steps, dtype=torch.float64, device=pr.device)
+                tk_extract(solver.h, k, re, im)
+                out.append(torch.stack([re, im], dim=1))
+            return torch.stack(out, dim=0)
+
+        @staticmethod
+        def backward(ctx, g):
+            g = g.detach().contiguous()
+            ga = gM = gpr = gpi = None
+            if ctx.needs_input_grad[2] or ctx.needs_input_grad[3]:
+                grad = torch.empty((2, solver.Ntheta, solver.Nr), dtype=torch.float64, device=g.device)
+                tk_adjoint(solver.h, grad, dL_dwave=g)
+                gpr, gpi = grad[0], grad[1]
+            if ctx.needs_input_grad[0]:
+                ga = torch.tensor(tk_param_gradient(solver.h, 0, g), dtype=torch.float64,
+                                  device=g.device)
+            if ctx.needs_input_grad[1]:
+                gM = torch.tensor(tk_param_gradient(solver.h, 1, g), dtype=torch.float64,
+                                  device=g.device)
+            return ga, gM, gpr, gpi
+
+    return _WaveformsParams.apply(a, M, phi_re, phi_im)
+
+
 def waveforms(solver: "Solver", phi_re, phi_im, n_steps: int):
     """Differentiable map from the initial planes (CUDA float64 tensors
     [Ntheta][Nr], momentum for zero time derivative) to the waveforms of the

@@ -138,3 +138,40 @@ def test_refusals():
     with pytest.raises(tk.TkError):
         g.param_gradient(2, dw[:1])
     g.close()
+
+
+def test_autograd_through_spin_mass_and_pulse():
+    """waveforms_with_params: torch gradients of a misfit with respect to a, M
+    and the pulse amplitude against 4-point finite differences."""
+    import torch
+    import paper_1010_3816_gb300 as tk
+    w = BASE.with_(steps=160)
+    g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
+                  substeps=w.substeps)
+    g.precompute(w.a, w.M, w.s, w.m)
+    for r, t in w.observers:
+        g.add_observer(r, t)
+    re, _ = initial_planes(w)
+    shape = torch.tensor(re, device="cuda")
+    target = torch.tensor(np.stack([np.stack([x.real, x.imag], -1) for x in _target(w)]),
+                          device="cuda")
+
+    def loss(a, M, A):
+        W = tk.waveforms_with_params(g, a, M, w.s, w.m, A * shape, torch.zeros_like(shape), w.steps)
+        return ((W - target) ** 2).sum()
+
+    p = [torch.tensor(v, dtype=torch.float64, device="cuda", requires_grad=True)
+         for v in (w.a, w.M, 1.0)]
+    L = loss(*p)
+    L.backward()
+    for k in range(3):
+        h = 1e-3
+        vals = []
+        for d in (h, -h, 2 * h, -2 * h):
+            q = [x.detach().clone() for x in p]
+            q[k] += d
+            with torch.no_grad():
+                vals.append(loss(*q).item())
+        fd = (8 * (vals[0] - vals[1]) - (vals[2] - vals[3])) / (12 * h)
+        assert abs(p[k].grad.item() - fd) <= 1e-7 * abs(fd), (k, p[k].grad.item(), fd)
+    g.close()

@@ -74,7 +74,7 @@ def test_discrete_angular_spectrum_converges(oracle_mod, s, m, variable):
     for N in (32, 64, 128):
         ev = _top_eigs(_matrix(oracle_mod, s, m, variable, N), n)
         errs.append(np.max(np.abs(ev - exact)))
-    # survey values: s=-2, m=2 -> 4, 10, 18 (negated)
+    # s = -2, m = 2: the exact values are -(l-s)(l+s+1) = -4, -10, -18 for l = 2, 3, 4
     assert errs[-1] < 2e-2 * np.max(np.abs(exact))
     # second order: halving dtheta divides the error by ~4
     assert errs[0] / errs[1] > 3.3 and errs[1] / errs[2] > 3.3, errs
