@@ -55,7 +55,7 @@ def _eq1_sympy(M, a, s, m, variable):
     else:
         w = sp.Integer(1)
     Psi = sp.exp(I * m * ph) * r ** 3 * w * Phi
-    # Eq. 1 (Sec. 3.1), term by term as printed
+    # Eq. 1 (Sec. 3.1), term by term
     e1 = (-((r ** 2 + as_ ** 2) ** 2 / Delta - as_ ** 2 * sp.sin(th) ** 2) * sp.diff(Psi, t, 2)
           - (4 * Ms * as_ * r / Delta) * sp.diff(Psi, t, ph)
           - 2 * s * (r - Ms * (r ** 2 - as_ ** 2) / Delta + I * as_ * sp.cos(th)) * sp.diff(Psi, t)
