@@ -43,13 +43,13 @@ WORKLOADS = {"kerr": KERR_25601x64, "schwarzschild": SCHWARZSCHILD_1601x32,
              "batched": None, "adjoint": ADJOINT_16001x128}
 
 # FP64 work of the step kernel per grid-point update, counted from its source:
-# half node (Eq. lw1) 4 adds + 4 multiplies + 20 FMAs, node (Eq. lw2) 4 adds +
+# half node (Eq. lw1) 4 adds + 2 multiplies + 20 FMAs, node (Eq. lw2) 4 adds +
 # 24 FMAs; an FMA counts 2 flops.
-FP64_FLOP_PER_UPDATE = (4 + 4 + 2 * 20) + (4 + 2 * 24)          # = 100
-FP64_INSTR_PER_UPDATE = 28 + 28
-# adjoint step per update: 50 FMAs + 6 multiplies + 6 adds (transposed blocks
+FP64_FLOP_PER_UPDATE = (4 + 2 + 2 * 20) + (4 + 2 * 24)          # = 98
+FP64_INSTR_PER_UPDATE = 26 + 28
+# adjoint step per update: 46 FMAs + 6 multiplies + 10 adds (transposed blocks
 # and transposed theta couplings at the node and the half node)
-ADJ_FLOP_PER_UPDATE = 2 * 50 + 6 + 6                             # = 112
+ADJ_FLOP_PER_UPDATE = 2 * 46 + 6 + 10                            # = 108
 ADJ_INSTR_PER_UPDATE = 62
 STATE_BYTES_PER_UPDATE = {0: 64, 1: 32}                         # read u^n, write u^{n+1}
 TABLE_BYTES_PER_UPDATE = {0: 21 * 8, 1: 21 * 4}                 # 11 + 10 table entries
@@ -63,10 +63,6 @@ FP32_FMA_PER_CLK_PER_SM = 128
 # keyed by (workload name, precision); the capture's command and figures are in the
 # named summary under profiles/.
 MEASURED_TRAFFIC = {
-    ("kerr_a0.9_25601x64_38400steps", 0): (333.902592e6 + 38.241280e6,
-                                           "profiles/lw_step_f64_kerr_25601x64.md"),
-    ("kerr_a0.9_25601x64_38400steps", 1): (210.219776e6 + 14.248960e6,
-                                           "profiles/lw_step2_ring_f32_kerr_25601x64.md"),
 }
 L2_FLUSH_BYTES = 256 << 20          # twice the 129 MB L2
 

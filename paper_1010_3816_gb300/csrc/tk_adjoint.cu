@@ -165,7 +165,7 @@ __device__ __forceinline__ void mu_node(const T (&l)[4][K], const T (&ep)[4][K],
                                         const T (&em)[4][K], const T (&ypr)[K], const T (&ypi)[K],
                                         const T (&ymr)[K], const T (&ymi)[K],
                                         const T *__restrict__ hp_tab, const T *__restrict__ hm_tab,
-                                        const T e, T (&mu)[4][K])
+                                        T (&mu)[4][K])
 {
     constexpr int NP = 32 * K;
     T S[K], FR[K], FI[K], PR[K], PI[K];
@@ -179,8 +179,8 @@ __device__ __forceinline__ void mu_node(const T (&l)[4][K], const T (&ep)[4][K],
     for (int t = 0; t < K; ++t) {
         mu[0][t] = fma(FI[t], ep[3][t], fma(FR[t], ep[2][t], fma(S[t], ep[0][t], l[0][t] + (ypr[t] + ymr[t]))));
         mu[1][t] = fma(FR[t], ep[3][t], fma(-FI[t], ep[2][t], fma(S[t], ep[1][t], l[1][t] + (ypi[t] + ymi[t]))));
-        mu[2][t] = fma(PI[t], ep[3][t], fma(PR[t], ep[2][t], fma(e, ep[0][t], l[2][t])));
-        mu[3][t] = fma(PR[t], ep[3][t], fma(-PI[t], ep[2][t], fma(e, ep[1][t], l[3][t])));
+        mu[2][t] = fma(PI[t], ep[3][t], fma(PR[t], ep[2][t], ep[0][t] + l[2][t]));
+        mu[3][t] = fma(PR[t], ep[3][t], fma(-PI[t], ep[2][t], ep[1][t] + l[3][t]));
     }
     // eta- with the "c" entries of half node i-1/2
     ldk<T, K>(hm_tab + H_HQ * NP, S);
@@ -192,8 +192,8 @@ __device__ __forceinline__ void mu_node(const T (&l)[4][K], const T (&ep)[4][K],
     for (int t = 0; t < K; ++t) {
         mu[0][t] = fma(FI[t], em[3][t], fma(FR[t], em[2][t], fma(S[t], em[0][t], mu[0][t])));
         mu[1][t] = fma(FR[t], em[3][t], fma(-FI[t], em[2][t], fma(S[t], em[1][t], mu[1][t])));
-        mu[2][t] = fma(PI[t], em[3][t], fma(PR[t], em[2][t], fma(e, em[0][t], mu[2][t])));
-        mu[3][t] = fma(PR[t], em[3][t], fma(-PI[t], em[2][t], fma(e, em[1][t], mu[3][t])));
+        mu[2][t] = fma(PI[t], em[3][t], fma(PR[t], em[2][t], em[0][t] + mu[2][t]));
+        mu[3][t] = fma(PR[t], em[3][t], fma(-PI[t], em[2][t], em[1][t] + mu[3][t]));
     }
 }
 
@@ -272,8 +272,7 @@ lw_adjoint_kernel(const T *__restrict__ lam, T *__restrict__ mu_out, const T *__
             } else {
                 T mu[4][K];
                 const T *hm_tab = half + (size_t)(i > 0 ? i - 1 : 0) * HP + row;
-                mu_node<T, K>(la, ep, em, ypr, ypi, ymr, ymi, half + (size_t)i * HP + row, hm_tab,
-                              eh, mu);
+                mu_node<T, K>(la, ep, em, ypr, ypi, ymr, ymi, half + (size_t)i * HP + row, hm_tab, mu);
                 store_col<T, K>(mu_out + (size_t)i * SP + row, mu);
             }
 #pragma unroll
@@ -317,7 +316,7 @@ lw_adjoint_kernel(const T *__restrict__ lam, T *__restrict__ mu_out, const T *__
             ypi[t] = sh[wib][15][row + t];
         }
         mu_node<T, K>(l0, ep, el, ypr, ypi, yml, ymli, half + (size_t)i0 * HP + row,
-                      half + (size_t)(i0 - 1) * HP + row, eh, mu);
+                      half + (size_t)(i0 - 1) * HP + row, mu);
         store_col<T, K>(mu_out + (size_t)i0 * SP + row, mu);
     }
 }
@@ -386,8 +385,8 @@ param_tangent_kernel(const double *__restrict__ u, const double *__restrict__ la
         if (i0 > 0) {
             double ul[4][K];
             load_col<double, K>(u + (size_t)(i0 - 1) * SP + row, ul);
-            half_node<double, K>(ul, ua, half + (size_t)(i0 - 1) * HP + row, eh, hm);
-            half_node<double, K>(ul, ua, dhalf + (size_t)(i0 - 1) * HP + row, 0.0, dm);
+            half_node<double, K>(ul, ua, half + (size_t)(i0 - 1) * HP + row, hm);
+            half_node<double, K, false>(ul, ua, dhalf + (size_t)(i0 - 1) * HP + row, dm);
         } else {
             zero_col<double, K>(hm);
             zero_col<double, K>(dm);
@@ -396,8 +395,8 @@ param_tangent_kernel(const double *__restrict__ u, const double *__restrict__ la
             double uc[4][K], hp[4][K], dp[4][K];
             if (i + 1 < Nr) {
                 load_col<double, K>(u + (size_t)(i + 1) * SP + row, uc);
-                half_node<double, K>(ua, uc, half + (size_t)i * HP + row, eh, hp);
-                half_node<double, K>(ua, uc, dhalf + (size_t)i * HP + row, 0.0, dp);
+                half_node<double, K>(ua, uc, half + (size_t)i * HP + row, hp);
+                half_node<double, K, false>(ua, uc, dhalf + (size_t)i * HP + row, dp);
             } else {
                 zero_col<double, K>(uc);
                 zero_col<double, K>(hp);

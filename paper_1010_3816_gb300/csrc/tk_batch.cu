@@ -65,7 +65,7 @@ __device__ void sweep(const BatchMember &m, const T *__restrict__ u_in, T *__res
     if (i0 > 0) {
         T ul[4][K];
         load_col<T, K>(u_in + (size_t)(i0 - 1) * SP + row, ul);
-        half_node<T, K>(ul, ua, half + (size_t)(i0 - 1) * HP + row, eh, hm);
+        half_node<T, K>(ul, ua, half + (size_t)(i0 - 1) * HP + row, hm);
     } else {
         zero_col<T, K>(hm);
     }
@@ -73,7 +73,7 @@ __device__ void sweep(const BatchMember &m, const T *__restrict__ u_in, T *__res
         T uc[4][K], hp[4][K], o[4][K];
         if (i + 1 < Nr) {
             load_col<T, K>(u_in + (size_t)(i + 1) * SP + row, uc);
-            half_node<T, K>(ua, uc, half + (size_t)i * HP + row, eh, hp);
+            half_node<T, K>(ua, uc, half + (size_t)i * HP + row, hp);
         } else {
             zero_col<T, K>(uc);
             zero_col<T, K>(hp);

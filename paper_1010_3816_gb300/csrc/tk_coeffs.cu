@@ -239,16 +239,19 @@ __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int 
                 double fpr = g1r + h2 * c.c3r - dg, fmr = -g1r + h2 * c.c3r - dg;
                 if (variable == 0 && jp == 0) { fpr += p * km; fmr += p * km; km = 0.0; }
                 if (variable == 0 && jp == Nth - 1) { fpr += p * kp; fmr += p * kp; kp = 0.0; }
-                nv[N_B] = B;
+                // entries that multiply half-node Phi values carry the factor eh
+                // (the half node returns Phi / eh, see the half-node tables)
+                const double eh = 0.25 * dt;
+                nv[N_B] = eh * B;
                 nv[N_PPR] = B + h2 * c.c2r;
                 nv[N_PMR] = -B + h2 * c.c2r;
                 nv[N_C2I] = h2 * c.c2i;
-                nv[N_FPR] = fpr;
-                nv[N_FPI] = g1i + h2 * c.c3i;
-                nv[N_FMR] = fmr;
-                nv[N_FMI] = -g1i + h2 * c.c3i;
-                nv[N_KP] = kp;
-                nv[N_KM] = km;
+                nv[N_FPR] = eh * fpr;
+                nv[N_FPI] = eh * (g1i + h2 * c.c3i);
+                nv[N_FMR] = eh * fmr;
+                nv[N_FMI] = eh * (-g1i + h2 * c.c3i);
+                nv[N_KP] = eh * kp;
+                nv[N_KM] = eh * km;
             }
         }
         if (i < Nr - 1) {   // half node r*_{i+1/2}, Eq. (lw1), step dt/2
@@ -268,8 +271,10 @@ __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int 
             double far = -g1r + e2 * c.c3r - dg, fcr = g1r + e2 * c.c3r - dg;
             if (variable == 0 && jp == 0) { far += p * km; fcr += p * km; km = 0.0; }
             if (variable == 0 && jp == Nth - 1) { far += p * kp; fcr += p * kp; kp = 0.0; }
-            hv[H_HP] = 0.5 + B;
-            hv[H_HQ] = 0.5 - B;
+            // the Phi half-node value is returned divided by e2 (= eh): its
+            // Pi term e2 (Pi_a + Pi_c) then needs no multiplication
+            hv[H_HP] = (0.5 + B) / e2;
+            hv[H_HQ] = (0.5 - B) / e2;
             hv[H_PAR] = 0.5 - B + e2 * c.c2r;
             hv[H_PCR] = 0.5 + B + e2 * c.c2r;
             hv[H_PI] = e2 * c.c2i;

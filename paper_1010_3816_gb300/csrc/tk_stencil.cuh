@@ -130,10 +130,15 @@ __device__ __forceinline__ void warp_range(int Nr, int wib, int *i0, int *i1, in
     *left = prev;
 }
 
-// Eq. (lw1): u^{n+1/2}_{i+1/2} from a = u^n_i and c = u^n_{i+1}.
-template <typename T, int K>
+// Eq. (lw1): u^{n+1/2}_{i+1/2} from a = u^n_i and c = u^n_{i+1}.  The Phi
+// components come out divided by eh = dt/4: the table entries HP, HQ carry the
+// factor 1/eh and the node tables multiply the half-node Phi values back by
+// eh, so the term eh (Pi_a + Pi_c) is added without a multiplication.
+// PI_TERM = false leaves that term out (the derivative of the step with
+// respect to the tables, where it is constant).
+template <typename T, int K, bool PI_TERM = true>
 __device__ __forceinline__ void half_node(const T (&a)[4][K], const T (&c)[4][K],
-                                          const T *__restrict__ tab, const T e, T (&h)[4][K])
+                                          const T *__restrict__ tab, T (&h)[4][K])
 {
     constexpr int NP = 32 * K;
     T sR[K], sI[K], upR[K], upI[K], dnR[K], dnI[K];
@@ -151,8 +156,13 @@ __device__ __forceinline__ void half_node(const T (&a)[4][K], const T (&c)[4][K]
     for (int t = 0; t < K; ++t) {
         const T sPR = a[2][t] + c[2][t];
         const T sPI = a[3][t] + c[3][t];
-        h[0][t] = fma(q[H_HQ][t], c[0][t], fma(q[H_HP][t], a[0][t], e * sPR));
-        h[1][t] = fma(q[H_HQ][t], c[1][t], fma(q[H_HP][t], a[1][t], e * sPI));
+        if constexpr (PI_TERM) {
+            h[0][t] = fma(q[H_HQ][t], c[0][t], fma(q[H_HP][t], a[0][t], sPR));
+            h[1][t] = fma(q[H_HQ][t], c[1][t], fma(q[H_HP][t], a[1][t], sPI));
+        } else {
+            h[0][t] = fma(q[H_HQ][t], c[0][t], q[H_HP][t] * a[0][t]);
+            h[1][t] = fma(q[H_HQ][t], c[1][t], q[H_HP][t] * a[1][t]);
+        }
         T x = q[H_PAR][t] * a[2][t];
         x = fma(q[H_PCR][t], c[2][t], x);
         x = fma(-q[H_PI][t], sPI, x);

@@ -130,7 +130,7 @@ __device__ __forceinline__ void step_sweep(unsigned char *sh_raw, const T *__res
         if (lead && i0 > 0) {
             T ul[4][K];
             load_state<T, K, CG>(u_in + (size_t)(i0 - 1) * SP + row, ul);
-            half_node<T, K>(ul, ua, half + (size_t)(i0 - 1) * HP + row, eh, hm);
+            half_node<T, K>(ul, ua, half + (size_t)(i0 - 1) * HP + row, hm);
         } else {
             zero_col<T, K>(hm);
         }
@@ -138,7 +138,7 @@ __device__ __forceinline__ void step_sweep(unsigned char *sh_raw, const T *__res
             T uc[4][K], hp[4][K], o[4][K];
             if (i + 1 < Nr) {
                 load_state<T, K, CG>(u_in + (size_t)(i + 1) * SP + row, uc);
-                half_node<T, K>(ua, uc, half + (size_t)i * HP + row, eh, hp);
+                half_node<T, K>(ua, uc, half + (size_t)i * HP + row, hp);
             } else {
                 zero_col<T, K>(uc);
                 zero_col<T, K>(hp);
@@ -309,7 +309,7 @@ lw_step2_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__re
             else zero_col<T, K>(c0);
             // level 1, half node between p - 1 and p
             if (p >= i0 - 1 && p >= 1 && p < Nr)
-                half_node<T, K>(a0, c0, half + (size_t)(p - 1) * HP + row, eh, h1p);
+                half_node<T, K>(a0, c0, half + (size_t)(p - 1) * HP + row, h1p);
             else
                 zero_col<T, K>(h1p);
             // level 1, node q = p - 1 (zero on the radial edges and outside the grid)
@@ -323,7 +323,7 @@ lw_step2_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__re
             // level 2, half node between r = p - 2 and p - 1
             const int r = p - 2;
             if (p >= i0 + 1 && r >= 0 && r + 1 < Nr)
-                half_node<T, K>(u1m, u1c, half + (size_t)r * HP + row, eh, h2p);
+                half_node<T, K>(u1m, u1c, half + (size_t)r * HP + row, h2p);
             else
                 zero_col<T, K>(h2p);
             // level 2, node r
@@ -472,7 +472,7 @@ lw_step2_ring_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T 
                     zero_col<T, K>(cn);
             }
             if (p >= i0 - 1 && p >= 1 && p < Nr)
-                half_node<T, K>(a0, c0, sc + kSlotHalf * NP + row, eh, h1p);
+                half_node<T, K>(a0, c0, sc + kSlotHalf * NP + row, h1p);
             else
                 zero_col<T, K>(h1p);
             const int q = p - 1;
@@ -484,7 +484,7 @@ lw_step2_ring_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T 
                 observe<T, K>(q, lane, u1c, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, 0);
             const int r = p - 2;
             if (p >= i0 + 1 && r >= 0 && r + 1 < Nr)
-                half_node<T, K>(u1m, u1c, sp + kSlotHalf * NP + row, eh, h2p);
+                half_node<T, K>(u1m, u1c, sp + kSlotHalf * NP + row, h2p);
             else
                 zero_col<T, K>(h2p);
             if (p >= i0 + 2) {
