@@ -63,6 +63,10 @@ FP32_FMA_PER_CLK_PER_SM = 128
 # keyed by (workload name, precision); the capture's command and figures are in the
 # named summary under profiles/.
 MEASURED_TRAFFIC = {
+    ("kerr_a0.9_25601x64_38400steps", 0): (333.903360e6 + 37.704704e6,
+                                           "profiles/lw_step_f64_kerr_25601x64.md"),
+    ("kerr_a0.9_25601x64_38400steps", 1): (210.242816e6 + 14.580736e6,
+                                           "profiles/lw_step2_ring_f32_kerr_25601x64.md"),
 }
 L2_FLUSH_BYTES = 256 << 20          # twice the 129 MB L2
 
