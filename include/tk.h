@@ -130,11 +130,15 @@ tk_status tk_add_observer(tk_solver *S, double rstar_obs, double theta_obs, int 
 
 /* Advance n >= 0 outer steps (Eqs. lw1 then lw2, with the theta-pole ghosts
  * and radial-edge zeros folded in), appending one sample per observer per
- * outer step.  Asynchronous.  Whole chunks of outer steps are replayed from a
- * CUDA graph captured on first use (see tk_set_graph_chunk); the rest are
- * launched one by one.  Both paths run the same kernels and give identical
- * results.  The first call after tk_add_observer, or after the waveform
- * buffer grew, captures a new graph (host work of ~1 ms). */
+ * outer step.  Asynchronous, except in the persistent mode of
+ * tk_set_steps_per_launch (-1, the default for FP64 grids too small for one
+ * block per SM), where every step of the call runs in one cooperative launch
+ * and the call synchronizes the stream to check that launch's bounded waits
+ * (TK_ERR_INTERNAL if one ran out; the state is then invalid).  Otherwise
+ * whole chunks of outer steps are replayed from a CUDA graph captured on
+ * first use (see tk_set_graph_chunk) and the rest are launched one by one.
+ * Every path gives identical results.  The first call after tk_add_observer,
+ * or after the waveform buffer grew, captures a new graph (host work of ~1 ms). */
 tk_status tk_step(tk_solver *S, int n);
 
 /* Outer steps per CUDA-graph replay in tk_step: -1 (default) picks about 64
