@@ -131,10 +131,11 @@ tk_status tk_add_observer(tk_solver *S, double rstar_obs, double theta_obs, int 
 /* Advance n >= 0 outer steps (Eqs. lw1 then lw2, with the theta-pole ghosts
  * and radial-edge zeros folded in), appending one sample per observer per
  * outer step.  Asynchronous, except in the persistent mode of
- * tk_set_steps_per_launch (-1, the default for FP64 grids too small for one
- * block per SM), where every step of the call runs in one cooperative launch
- * and the call synchronizes the stream to check that launch's bounded waits
- * (TK_ERR_INTERNAL if one ran out; the state is then invalid).  Otherwise
+ * tk_set_steps_per_launch (-1, the default for FP32 and for FP64 grids too
+ * small for one block per SM), where every step of the call runs in one
+ * cooperative launch and the call synchronizes the stream to check that
+ * launch's bounded waits (TK_ERR_INTERNAL if one ran out; the state is then
+ * invalid).  Otherwise
  * whole chunks of outer steps are replayed from a CUDA graph captured on
  * first use (see tk_set_graph_chunk) and the rest are launched one by one.
  * Every path gives identical results.  The first call after tk_add_observer,
@@ -235,10 +236,11 @@ tk_status tk_stability_bound(tk_solver *S, double growth_per_step, double *dt_ma
                              int *substeps_needed);
 
 /* Lax-Wendroff steps per kernel launch: 1, 2, -1 (every inner step of a
- * tk_step call in one persistent launch), or 0 for the default: 2 for
- * TK_PREC_F32, whose step is bound by memory traffic; for TK_PREC_F64, whose
- * step is bound by FP64 arithmetic, 1, or -1 on grids too small for one block
- * per SM (where launch overhead and latency dominate).  With 2,
+ * tk_step call in one persistent launch: single steps for TK_PREC_F64, pairs
+ * for TK_PREC_F32), or 0 for the default: -1 for TK_PREC_F32, whose step is
+ * bound by memory traffic; for TK_PREC_F64, whose step is bound by FP64
+ * arithmetic, 1, or -1 on grids too small for one block per SM (where launch
+ * overhead and latency dominate).  With 2,
  * pairs of inner steps run in one launch that reads the state and the
  * coefficient tables once; each warp recomputes the intermediate level one
  * column beyond its range, which adds arithmetic but no DRAM traffic.  With
@@ -246,7 +248,7 @@ tk_status tk_stability_bound(tk_solver *S, double growth_per_step, double *dt_ma
  * every step for its two neighbouring blocks; the waits are bounded, and
  * tk_step then synchronizes the stream and returns TK_ERR_INTERNAL if one
  * ran out.  Results are bit-identical in every mode.  Returns TK_ERR_ARG for
- * other values, and for -1 on a grid that fills the GPU. */
+ * other values. */
 tk_status tk_set_steps_per_launch(tk_solver *S, int steps);
 
 /* Lax-Wendroff steps per outer step in use (the count chosen at the last

@@ -136,15 +136,23 @@ using tkh::fail;
 constexpr double kAutoGrowthPerStep = 2.5e-5;
 
 // Launch structure for tk_step.  mode 0 (automatic): FP32, bound by memory,
-// takes two steps per launch; FP64, bound by its arithmetic (which the
-// two-step kernel's overlap adds to), takes one, and on grids too small for
-// one block per SM runs every step of a call in one persistent launch (per
-// step launch overhead and latency dominate there; measured 6 % faster on the
-// 1601 x 32 grid, while FP32 is faster with its two-step launches).
+// runs every step of a call as pairs of steps in one persistent launch (two
+// steps per read of the state and the tables, and no per-launch tail: a
+// block waits only for its neighbours, so random differences in block speed
+// average out); FP64, bound by its arithmetic (which the two-step kernel's
+// overlap adds to), takes one step per launch, and every step of a call in
+// one persistent launch on grids too small for one block per SM (where
+// launch overhead and latency dominate).  Measured: FP32 25601 x 64, 16.5
+// against 18.3 us per step with a launch per pair; FP64 1601 x 32, 9.1
+// against 9.7 us; FP64 25601 x 64, 155.3 against 155.5 us (not worth the
+// host synchronization the persistent launch needs).
 static void set_launch_mode(tk_solver *S, int mode)
 {
     S->fuse_mode = mode;
-    if (mode == 0) mode = S->precision == TK_PREC_F32 ? 2 : (S->persist_blocks > 0 ? -1 : 1);
+    if (mode == 0) {
+        if (S->precision == TK_PREC_F32) mode = S->persist_blocks > 0 ? -1 : 2;
+        else mode = (S->persist_blocks > 0 && S->warps == tk::kNarrowWarps) ? -1 : 1;
+    }
     S->persist = (mode == -1);
     S->fuse = (mode == 2);
 }
@@ -196,8 +204,11 @@ tk_status tk_make_grid(tk_solver **out, double rstar_min, double rstar_max, int 
     S->blocks = tk::step_grid_shape(precision, S->K, Nr, S->num_sms, &S->warps);
     S->adj_blocks = tk::adjoint_grid_shape(precision, S->K, Nr, S->num_sms, &S->adj_warps);
     S->fused_blocks = tk::fused_grid_shape(precision, S->K, Nr, S->num_sms, &S->fused_warps);
-    S->persist_blocks = (S->warps == tk::kNarrowWarps)
-                            ? tk::persistent_grid_blocks(precision, S->K, Nr, S->num_sms) : 0;
+    // the persistent launch: FP64 runs the one-step kernel's grid, FP32 the
+    // two-step (ring) kernel's, both one wave of resident blocks
+    S->persist_blocks = (precision == TK_PREC_F32)
+                            ? S->fused_blocks
+                            : tk::persistent_grid_blocks(precision, S->K, Nr, S->num_sms, S->warps);
     set_launch_mode(S, 0);
 
     const size_t se = state_elems(S);
@@ -487,27 +498,44 @@ tk_status tk_step(tk_solver *S, int n)
     if (S->persist && (long long)n * S->substeps >= 2) {
         // every inner step of the call in one cooperative launch; its waits
         // are bounded, and a wait that timed out is reported here
+        const size_t fbytes = (size_t)S->persist_blocks * sizeof(unsigned int) + sizeof(int);
         if (!S->pflags) {
-            st = alloc(S, (void **)&S->pflags, (size_t)S->persist_blocks * sizeof(unsigned int) + sizeof(int));
+            st = alloc(S, (void **)&S->pflags, fbytes);
             if (st != TK_OK) return st;
         }
         int *perr = (int *)(S->pflags + S->persist_blocks);
-        TK_CUDA(S, cudaMemsetAsync(S->pflags, 0, (size_t)S->persist_blocks * sizeof(unsigned int) + sizeof(int),
-                                   S->stream));
+        TK_CUDA(S, cudaMemsetAsync(S->pflags, 0, fbytes, S->stream));
         tk::StepLaunch L;
         tkh::fill_launch(S, L);
         L.blocks = S->persist_blocks;
-        L.warps = tk::kNarrowWarps;
+        L.warps = S->precision == TK_PREC_F32 ? S->fused_warps : S->warps;
         L.u_in = S->u[S->cur];
         L.write_wave = S->nobs > 0;
         const long long inner = (long long)n * S->substeps;
         if (inner > 0x7fffffff) return fail(S, TK_ERR_ARG, "tk_step: %d outer steps are too many for one call", n);
-        TK_CUDA(S, tk::launch_lw_persistent(L, S->u[S->cur ^ 1], (int)inner, S->substeps, S->pflags, perr,
-                                            S->stream));
+        if (S->precision == TK_PREC_F32) {
+            // pairs of steps in one launch; an odd last step by the one-step kernel
+            const long long pairs = inner / 2;
+            TK_CUDA(S, tk::launch_ring_persistent(L, S->u[S->cur ^ 1], (int)pairs, S->substeps, S->pflags,
+                                                  perr, S->stream));
+            if (pairs & 1) S->cur ^= 1;
+            if (inner & 1) {
+                tk::StepLaunch L1;
+                tkh::fill_launch(S, L1);
+                L1.u_in = S->u[S->cur];
+                L1.u_out = S->u[S->cur ^ 1];
+                L1.write_wave = S->nobs > 0;
+                TK_CUDA(S, tk::launch_lw_step(L1, S->stream));
+                S->cur ^= 1;
+            }
+        } else {
+            TK_CUDA(S, tk::launch_lw_persistent(L, S->u[S->cur ^ 1], (int)inner, S->substeps, S->pflags,
+                                                perr, S->stream));
+            if (inner & 1) S->cur ^= 1;
+        }
         int herr = 0;
         TK_CUDA(S, cudaMemcpyAsync(&herr, perr, sizeof(int), cudaMemcpyDeviceToHost, S->stream));
         TK_CUDA(S, cudaStreamSynchronize(S->stream));
-        if (inner & 1) S->cur ^= 1;
         S->count += n;
         S->steps_done += n;
         if (herr)
@@ -543,7 +571,7 @@ tk_status tk_set_steps_per_launch(tk_solver *S, int steps)
         return fail(S, TK_ERR_ARG, "tk_set_steps_per_launch: %d is not -1, 0, 1 or 2", steps);
     if (steps == -1 && S->persist_blocks == 0)
         return fail(S, TK_ERR_ARG, "tk_set_steps_per_launch: this grid cannot run as one "
-                                   "persistent launch (it fills the GPU with one block per SM)");
+                                   "persistent launch");
     set_launch_mode(S, steps);
     S->epoch++;
     return TK_OK;

@@ -116,9 +116,13 @@ int step_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
 // 0 if it cannot run; the launch itself (L.u_in holds u^n, u_other is the
 // second level; flags: one zeroed unsigned int per block; *err set on a wait
 // that timed out).
-int persistent_grid_blocks(int precision, int K, int Nr, int num_sms);
+int persistent_grid_blocks(int precision, int K, int Nr, int num_sms, int warps);
 cudaError_t launch_lw_persistent(const StepLaunch &L, void *u_other, int n_inner, int substeps,
                                  unsigned int *flags, int *err, cudaStream_t st);
+// Pairs of steps in one cooperative launch (FP32, the two-step kernel's grid
+// and shared-memory ring): L.u_in holds u^n, u_other the second level.
+cudaError_t launch_ring_persistent(const StepLaunch &L, void *u_other, int n_pairs, int k,
+                                   unsigned int *flags, int *err, cudaStream_t st);
 // Launch shape of the two-step kernel.
 int fused_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
 // Launch shape of the adjoint step kernel: returns the number of blocks and

@@ -371,18 +371,13 @@ lw_step2_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__re
 // column and the load latency of column p + 1 overlaps the arithmetic of
 // column p.  The arithmetic is that of lw_step2_kernel.
 constexpr int kRingSlots = 3;
-// The state column either goes through the ring with the tables (more
-// shared memory per warp, fewer warps per SM) or is loaded into registers
-// one column ahead (less shared memory, more warps).
-constexpr bool kRingStagesState = false;
-constexpr int kSlotCols = (kRingStagesState ? 4 : 0) + kNCH + kNCN;
-constexpr int kSlotHalf = kRingStagesState ? 4 : 0;          // offset of the half-node table
-constexpr int kSlotNode = kSlotHalf + kNCH;                   // offset of the node table
+constexpr int kSlotCols = kNCH + kNCN;   // half-node table, node table
+constexpr int kSlotNode = kNCH;          // offset of the node table in a slot
 
 template <typename T, int K>
 constexpr int ring_warps()
 {
-    return kRingStagesState ? (K == 1 ? 20 : K == 2 ? 8 : 4) : (K == 1 ? 24 : K == 2 ? 12 : 4);
+    return K == 1 ? 24 : K == 2 ? 12 : 4;
 }
 
 template <typename T, int K>
@@ -406,22 +401,18 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Issue the copies of column p (state u_p, tables half_{p-1}, node_{p-1}, the
-// level-1 operands at step p of the sweep) into `slot`, then commit a group
-// (empty where the column is outside the grid).
+// Issue the copies of the first-level tables of sweep step p (half_{p-1},
+// node_{p-1}) into `slot`, then commit a group (empty where the column is
+// outside the grid).
 template <typename T, int K>
-__device__ __forceinline__ void ring_fetch(T *slot, const T *__restrict__ u, const T *__restrict__ half,
+__device__ __forceinline__ void ring_fetch(T *slot, const T *__restrict__ half,
                                            const T *__restrict__ node, int p, int Nr, int row)
 {
     constexpr int NP = 32 * K, B = K * (int)sizeof(T);
-    if (kRingStagesState && p >= 0 && p < Nr) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) cp_async<B>(slot + c * NP + row, u + ((size_t)p * 4 + c) * NP + row);
-    }
     if (p >= 1 && p < Nr) {
 #pragma unroll
         for (int q = 0; q < kNCH; ++q)
-            cp_async<B>(slot + (kSlotHalf + q) * NP + row, half + ((size_t)(p - 1) * kNCH + q) * NP + row);
+            cp_async<B>(slot + q * NP + row, half + ((size_t)(p - 1) * kNCH + q) * NP + row);
 #pragma unroll
         for (int q = 0; q < kNCN; ++q)
             cp_async<B>(slot + (kSlotNode + q) * NP + row, node + ((size_t)(p - 1) * kNCN + q) * NP + row);
@@ -429,60 +420,56 @@ __device__ __forceinline__ void ring_fetch(T *slot, const T *__restrict__ u, con
     cp_async_commit();
 }
 
-template <typename T, int K, int W>
-__global__ void __launch_bounds__(W * 32, 1)
-lw_step2_ring_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__restrict__ half,
-                     const T *__restrict__ node, int Nr, T eh, T en, const WaveArgs wa, int obs_mask)
+// The two-step sweep over the block's columns (the body of the ring kernel).
+// mask: bit 0, an outer step ends after the first step, bit 1 after the
+// second; off1, off2: their samples after the counter's value.  CG: the state
+// is loaded from L2 (other blocks of the same launch wrote it).
+template <typename T, int K, int W, bool CG>
+__device__ __forceinline__ void ring_sweep(unsigned char *sh_raw, const T *__restrict__ u_in,
+                                           T *__restrict__ u_out, const T *__restrict__ half,
+                                           const T *__restrict__ node, int Nr, T en,
+                                           const WaveArgs &wa, int mask, int off1, int off2)
 {
     constexpr int NP = 32 * K;
     constexpr size_t SP = 4 * NP;
-    extern __shared__ __align__(16) unsigned char sh_raw[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     T *ring = reinterpret_cast<T *>(sh_raw) + (size_t)wib * kRingSlots * kSlotCols * NP;
     int i0, i1, left;
     warp_range<W>(Nr, wib, &i0, &i1, &left);
     const int row = lane * K;
-    const int second = obs_mask & 1;
     if (i1 > i0) {
         T a0[4][K], h1m[4][K], u1m[4][K], h2m[4][K];
         zero_col<T, K>(a0);
         zero_col<T, K>(h1m);
         zero_col<T, K>(u1m);
         zero_col<T, K>(h2m);
-        ring_fetch<T, K>(ring, u_in, half, node, i0 - 2, Nr, row);
-        T cn[4][K];   // the state column p + 1, loaded one column ahead (unstaged state)
-        if (!kRingStagesState) {
-            if (i0 - 2 >= 0) load_col<T, K>(u_in + (size_t)(i0 - 2) * SP + row, cn);
-            else zero_col<T, K>(cn);
-        }
+        ring_fetch<T, K>(ring, half, node, i0 - 2, Nr, row);
+        T cn[4][K];   // the state column p + 1, loaded one column ahead
+        if (i0 - 2 >= 0) load_state<T, K, CG>(u_in + (size_t)(i0 - 2) * SP + row, cn);
+        else zero_col<T, K>(cn);
         int cur = 0;
         for (int p = i0 - 2; p <= i1 + 1; ++p) {
             const int nxt = cur == kRingSlots - 1 ? 0 : cur + 1;
             const int prv = cur == 0 ? kRingSlots - 1 : cur - 1;
             if (p + 1 <= i1 + 1)
-                ring_fetch<T, K>(ring + nxt * kSlotCols * NP, u_in, half, node, p + 1, Nr, row);
+                ring_fetch<T, K>(ring + nxt * kSlotCols * NP, half, node, p + 1, Nr, row);
             else
                 cp_async_commit();
             cp_async_wait_one();
-            const T *sc = ring + cur * kSlotCols * NP;    // column p: u_p, half_{p-1}, node_{p-1}
-            const T *sp = ring + prv * kSlotCols * NP;    // column p - 1: half_{p-2}, node_{p-2}
+            const T *sc = ring + cur * kSlotCols * NP;    // tables of step p: half_{p-1}, node_{p-1}
+            const T *sp = ring + prv * kSlotCols * NP;    // of step p - 1: half_{p-2}, node_{p-2}
             T c0[4][K], h1p[4][K], u1c[4][K], h2p[4][K];
-            if (kRingStagesState) {
-                if (p >= 0 && p < Nr) load_col<T, K>(sc + row, c0);
-                else zero_col<T, K>(c0);
-            } else {
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
+            for (int c = 0; c < 4; ++c)
 #pragma unroll
-                    for (int t = 0; t < K; ++t) c0[c][t] = cn[c][t];
-                if (p + 1 >= 0 && p + 1 < Nr && p + 1 <= i1 + 1)
-                    load_col<T, K>(u_in + (size_t)(p + 1) * SP + row, cn);
-                else
-                    zero_col<T, K>(cn);
-            }
+                for (int t = 0; t < K; ++t) c0[c][t] = cn[c][t];
+            if (p + 1 >= 0 && p + 1 < Nr && p + 1 <= i1 + 1)
+                load_state<T, K, CG>(u_in + (size_t)(p + 1) * SP + row, cn);
+            else
+                zero_col<T, K>(cn);
             if (p >= i0 - 1 && p >= 1 && p < Nr)
-                half_node<T, K>(a0, c0, sc + kSlotHalf * NP + row, h1p);
+                half_node<T, K>(a0, c0, sc + row, h1p);
             else
                 zero_col<T, K>(h1p);
             const int q = p - 1;
@@ -490,11 +477,11 @@ lw_step2_ring_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T 
                 full_node<T, K>(h1m, h1p, a0, sc + kSlotNode * NP + row, en, u1c);
             else
                 zero_col<T, K>(u1c);
-            if ((obs_mask & 1) && q >= i0 && q < i1)
-                observe<T, K>(q, lane, u1c, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, 0);
+            if ((mask & 1) && q >= i0 && q < i1)
+                observe<T, K>(q, lane, u1c, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, off1);
             const int r = p - 2;
             if (p >= i0 + 1 && r >= 0 && r + 1 < Nr)
-                half_node<T, K>(u1m, u1c, sp + kSlotHalf * NP + row, h2p);
+                half_node<T, K>(u1m, u1c, sp + row, h2p);
             else
                 zero_col<T, K>(h2p);
             if (p >= i0 + 2) {
@@ -504,8 +491,8 @@ lw_step2_ring_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T 
                 else
                     zero_col<T, K>(o);
                 store_col<T, K>(u_out + (size_t)r * SP + row, o);
-                if (obs_mask & 2)
-                    observe<T, K>(r, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, second);
+                if (mask & 2)
+                    observe<T, K>(r, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, off2);
             }
 #pragma unroll
             for (int c = 0; c < 4; ++c)
@@ -520,7 +507,41 @@ lw_step2_ring_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T 
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     }
+}
+
+template <typename T, int K, int W>
+__global__ void __launch_bounds__(W * 32, 1)
+lw_step2_ring_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__restrict__ half,
+                     const T *__restrict__ node, int Nr, T eh, T en, const WaveArgs wa, int obs_mask)
+{
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    ring_sweep<T, K, W, false>(sh_raw, u_in, u_out, half, node, Nr, en, wa, obs_mask, 0, obs_mask & 1);
     if (obs_mask) advance_sample(wa, (obs_mask & 1) + ((obs_mask >> 1) & 1));
+}
+
+// The two-step sweep for many pairs of steps in one cooperative launch, the
+// blocks waiting only for their two neighbours between pairs (as in
+// lw_persistent_kernel): a block's columns need the two columns on each side
+// from its neighbours, and a block overwrites the level its neighbours read
+// in the previous pair.  Pair p takes inner steps 2p and 2p + 1 of the call;
+// an outer step of k inner steps that ends inside it is observed there.
+template <typename T, int K, int W>
+__global__ void __launch_bounds__(W * 32, 1)
+lw_ring_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__restrict__ node,
+                          int Nr, T en, const WaveArgs wa, int n_pairs, int k, unsigned int *flags,
+                          int *err)
+{
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    for (int p = 0; p < n_pairs; ++p) {
+        const T *in = (p & 1) ? u1 : u0;
+        T *out = (p & 1) ? u0 : u1;
+        const int t = 2 * p;
+        const int mask = wa.write ? (((t + 1) % k == 0) | (((t + 2) % k == 0) << 1)) : 0;
+        ring_sweep<T, K, W, true>(sh_raw, in, out, half, node, Nr, en, wa, mask, (t + 1) / k - 1,
+                                  (t + 2) / k - 1);
+        if (p + 1 < n_pairs && !neighbour_barrier(flags, (unsigned)(p + 1), err)) break;
+    }
+    if (wa.write) advance_sample(wa, (2 * n_pairs) / k);
 }
 
 template <typename T, int K, int W>
@@ -688,10 +709,9 @@ int fused_shape(int Nr, int num_sms, int *warps)
     return blocks < 1 ? 1 : blocks;
 }
 
-template <typename T, int K>
-int persistent_blocks(int Nr, int num_sms)
+template <typename T, int K, int W>
+int persistent_blocks_w(int Nr, int num_sms)
 {
-    constexpr int W = kNarrowWarps;
     int n = 0;
     if (step_smem_setup<T, K, W>() != cudaSuccess) return 0;
     static cudaError_t e0 = cudaFuncSetAttribute(lw_persistent_kernel<T, K, W>,
@@ -708,10 +728,18 @@ int persistent_blocks(int Nr, int num_sms)
 }
 
 template <typename T, int K>
-cudaError_t launch_persistent_typed(const StepLaunch &L, void *u_other, int n_inner, int substeps,
-                                    unsigned int *flags, int *err, cudaStream_t st)
+int persistent_blocks(int Nr, int num_sms, int warps)
 {
-    constexpr int W = kNarrowWarps;
+    constexpr int WW = wide_warps<T, K>();
+    if (warps == WW) return persistent_blocks_w<T, K, WW>(Nr, num_sms);
+    if (warps == kNarrowWarps) return persistent_blocks_w<T, K, kNarrowWarps>(Nr, num_sms);
+    return 0;
+}
+
+template <typename T, int K, int W>
+cudaError_t launch_persistent_w(const StepLaunch &L, void *u_other, int n_inner, int substeps,
+                                unsigned int *flags, int *err, cudaStream_t st)
+{
     WaveArgs wa;
     wa.write = L.write_wave;
     wa.sample = L.sample_ctr;
@@ -729,17 +757,77 @@ cudaError_t launch_persistent_typed(const StepLaunch &L, void *u_other, int n_in
                                        dim3(W * 32), args, step_smem_bytes<T, K, W>(), st);
 }
 
+template <typename T, int K>
+cudaError_t launch_persistent_typed(const StepLaunch &L, void *u_other, int n_inner, int substeps,
+                                    unsigned int *flags, int *err, cudaStream_t st)
+{
+    constexpr int WW = wide_warps<T, K>();
+    if (L.warps == WW)
+        return launch_persistent_w<T, K, WW>(L, u_other, n_inner, substeps, flags, err, st);
+    if (L.warps == kNarrowWarps)
+        return launch_persistent_w<T, K, kNarrowWarps>(L, u_other, n_inner, substeps, flags, err, st);
+    return cudaErrorInvalidValue;
+}
+
+template <typename T, int K, int W>
+cudaError_t launch_ring_persistent_w(const StepLaunch &L, void *u_other, int n_pairs, int k,
+                                     unsigned int *flags, int *err, cudaStream_t st)
+{
+    cudaError_t e = ring_smem_setup<T, K, W>();
+    if (e != cudaSuccess) return e;
+    static cudaError_t e0 = cudaFuncSetAttribute(lw_ring_persistent_kernel<T, K, W>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(ring_smem_bytes<T, K>() / ring_warps<T, K>() * W));
+    if (e0 != cudaSuccess) return e0;
+    WaveArgs wa;
+    wa.write = L.write_wave;
+    wa.sample = L.sample_ctr;
+    wa.done = L.done_ctr;
+    wa.cap = L.wave_cap;
+    wa.wave = L.wave;
+    wa.w_row = L.w_row;
+    wa.obs = L.obs;
+    T *u0 = (T *)L.u_in, *u1 = (T *)u_other;
+    const T *half = (const T *)L.half, *node = (const T *)L.node;
+    int Nr = L.Nr;
+    T en = (T)(0.5 * L.dt_inner);
+    void *args[] = {&u0, &u1, &half, &node, &Nr, &en, &wa, &n_pairs, &k, &flags, &err};
+    return cudaLaunchCooperativeKernel((const void *)lw_ring_persistent_kernel<T, K, W>, dim3(L.blocks),
+                                       dim3(W * 32), args,
+                                       ring_smem_bytes<T, K>() / ring_warps<T, K>() * W, st);
+}
+
+template <typename T, int K>
+cudaError_t launch_ring_persistent_typed(const StepLaunch &L, void *u_other, int n_pairs, int k,
+                                         unsigned int *flags, int *err, cudaStream_t st)
+{
+    constexpr int WR = ring_warps<T, K>();
+    if (L.warps == WR) return launch_ring_persistent_w<T, K, WR>(L, u_other, n_pairs, k, flags, err, st);
+    if (L.warps == kNarrowWarps)
+        return launch_ring_persistent_w<T, K, kNarrowWarps>(L, u_other, n_pairs, k, flags, err, st);
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
-int persistent_grid_blocks(int precision, int K, int Nr, int num_sms)
+cudaError_t launch_ring_persistent(const StepLaunch &L, void *u_other, int n_pairs, int k,
+                                   unsigned int *flags, int *err, cudaStream_t st)
+{
+    if (L.precision != 1) return cudaErrorInvalidValue;
+    if (L.K == 1) return launch_ring_persistent_typed<float, 1>(L, u_other, n_pairs, k, flags, err, st);
+    if (L.K == 2) return launch_ring_persistent_typed<float, 2>(L, u_other, n_pairs, k, flags, err, st);
+    return launch_ring_persistent_typed<float, 4>(L, u_other, n_pairs, k, flags, err, st);
+}
+
+int persistent_grid_blocks(int precision, int K, int Nr, int num_sms, int warps)
 {
     if (precision == 0)
-        return K == 1 ? persistent_blocks<double, 1>(Nr, num_sms)
-             : K == 2 ? persistent_blocks<double, 2>(Nr, num_sms)
-                      : persistent_blocks<double, 4>(Nr, num_sms);
-    return K == 1 ? persistent_blocks<float, 1>(Nr, num_sms)
-         : K == 2 ? persistent_blocks<float, 2>(Nr, num_sms)
-                  : persistent_blocks<float, 4>(Nr, num_sms);
+        return K == 1 ? persistent_blocks<double, 1>(Nr, num_sms, warps)
+             : K == 2 ? persistent_blocks<double, 2>(Nr, num_sms, warps)
+                      : persistent_blocks<double, 4>(Nr, num_sms, warps);
+    return K == 1 ? persistent_blocks<float, 1>(Nr, num_sms, warps)
+         : K == 2 ? persistent_blocks<float, 2>(Nr, num_sms, warps)
+                  : persistent_blocks<float, 4>(Nr, num_sms, warps);
 }
 
 cudaError_t launch_lw_persistent(const StepLaunch &L, void *u_other, int n_inner, int substeps,

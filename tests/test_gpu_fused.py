@@ -106,29 +106,25 @@ PERSISTENT_CASES = [
     (0, _grid(997, 40, substeps=1, variable=0, dt=0.01), (25,)),   # literal, padded rows
     (1, _grid(1601, 32, substeps=2), (13, 8)),
     (0, _grid(23, 8, substeps=1, observers=((-30.0, 1.5), (-29.0, 0.5))), (31,)),  # few columns
+    (0, _grid(2501, 64, substeps=2), (6, 3)),               # FP64, one 16-warp block per SM
+    (1, _grid(3001, 64, substeps=2), (7, 1, 4)),            # FP32 pairs, one 12-warp block per SM
+    (1, _grid(3001, 64, substeps=3), (5,)),                 # FP32, an odd last step
+    (1, _grid(5003, 32, substeps=1), (9,)),                 # FP32 K = 1
+    (1, _grid(1301, 128, substeps=4), (3,)),                # FP32 K = 4
 ]
 
 
 @pytest.mark.parametrize("precision,w,calls", PERSISTENT_CASES,
                          ids=[f"case{k}" for k in range(len(PERSISTENT_CASES))])
 def test_persistent_launch_bit_identical(precision, w, calls):
-    """All inner steps of each tk_step call in one cooperative launch, blocks
-    waiting on their neighbours between steps: the same bits as one launch per
-    step, waveforms included."""
+    """All inner steps of each tk_step call in one cooperative launch (FP64:
+    single steps; FP32: pairs of steps), blocks waiting on their neighbours in
+    between: the same bits as one launch per step, waveforms included."""
     s1, w1 = _run(w, precision, 1, calls)
     sp, wp = _run(w, precision, -1, calls)
     assert np.isfinite(s1).all()
     assert np.array_equal(s1, sp)
     assert all(np.array_equal(a, b) for a, b in zip(w1, wp))
-    # and the automatic choice (persistent for FP64 on these small grids)
+    # and the automatic choice
     s0, w0 = _run(w, precision, 0, calls)
     assert np.array_equal(s0, sp) and all(np.array_equal(a, b) for a, b in zip(w0, wp))
-
-
-def test_persistent_launch_refused_on_a_full_grid():
-    import paper_1010_3816_gb300 as tk
-    w = _grid(5003, 64)
-    g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt)
-    with pytest.raises(tk.TkError):
-        g.set_steps_per_launch(-1)
-    g.close()
