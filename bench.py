@@ -44,7 +44,9 @@ WORKLOADS = {"kerr": KERR_25601x64, "schwarzschild": SCHWARZSCHILD_1601x32,
 
 # FP64 work of the step kernel per grid-point update, counted from its source:
 # half node (Eq. lw1) 4 adds + 2 multiplies + 20 FMAs, node (Eq. lw2) 4 adds +
-# 24 FMAs; an FMA counts 2 flops.
+# 24 FMAs; an FMA counts 2 flops.  The adds and multiplies are issued as FMAs
+# with 1 and -0 (54 DFMA instructions), so at most 98 of the 108 flops a full
+# pipe would do are useful.
 FP64_FLOP_PER_UPDATE = (4 + 2 + 2 * 20) + (4 + 2 * 24)          # = 98
 FP64_INSTR_PER_UPDATE = 26 + 28
 # adjoint step per update: 46 FMAs + 6 multiplies + 10 adds (transposed blocks
@@ -64,8 +66,6 @@ FP32_FMA_PER_CLK_PER_SM = 128
 # keyed by (workload name, precision); the capture's command and figures are in the
 # named summary under profiles/.
 MEASURED_TRAFFIC = {
-    ("kerr_a0.9_25601x64_38400steps", 0): (333.903360e6 + 37.704704e6,
-                                           "profiles/lw_step_f64_kerr_25601x64.md"),
     # one launch of 100 pairs: 17.148580 + 2.553906 GB
     ("kerr_a0.9_25601x64_38400steps", 1): ((17.148580e9 + 2.553906e9) / 100,
                                            "profiles/lw_ring_persistent_f32_kerr_25601x64.md"),

@@ -80,6 +80,7 @@ template <typename T, int K>
 __device__ __forceinline__ void neighbour_in(const T (&kp)[K], const T (&km)[K], const T (&xr)[K],
                                              const T (&xi)[K], T (&outr)[K], T (&outi)[K])
 {
+    const FmaK<T> k1 = fma_k<T>();
     const int lane = threadIdx.x & 31;
     const T kp_prv = __shfl_up_sync(kFull, kp[K - 1], 1);
     const T km_nxt = __shfl_down_sync(kFull, km[0], 1);
@@ -92,8 +93,8 @@ __device__ __forceinline__ void neighbour_in(const T (&kp)[K], const T (&km)[K],
         T kmu = (t + 1 < K) ? km[t + 1] : km_nxt;
         if (t == 0 && lane == 0) kpd = T(0);
         if (t == K - 1 && lane == 31) kmu = T(0);
-        outr[t] = fma(kpd, xrd[t], kmu * xru[t]);
-        outi[t] = fma(kpd, xid[t], kmu * xiu[t]);
+        outr[t] = fma(kpd, xrd[t], fma(kmu, xru[t], k1.nz));
+        outi[t] = fma(kpd, xid[t], fma(kmu, xiu[t], k1.nz));
     }
 }
 
@@ -116,6 +117,7 @@ __device__ __forceinline__ void eta_half(const T (&la)[4][K], const T (&lc)[4][K
                                          const T (&zci)[K], const T *__restrict__ ta,
                                          const T *__restrict__ tc, const T E, T (&h)[4][K])
 {
+    const FmaK<T> k1 = fma_k<T>();
     constexpr int NP = 32 * K;
     T B[K], FR[K], FI[K], PR[K], CI[K];
     // left node: the half node is its h+ (coefficients -B, FP, PPR, C2I)
@@ -126,10 +128,10 @@ __device__ __forceinline__ void eta_half(const T (&la)[4][K], const T (&lc)[4][K
     ldk<T, K>(ta + N_C2I * NP, CI);
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-        h[0][t] = fma(FI[t], la[3][t], fma(FR[t], la[2][t], fma(-B[t], la[0][t], zar[t] + zcr[t])));
-        h[1][t] = fma(FR[t], la[3][t], fma(-FI[t], la[2][t], fma(-B[t], la[1][t], zai[t] + zci[t])));
-        h[2][t] = fma(CI[t], la[3][t], fma(PR[t], la[2][t], E * la[0][t]));
-        h[3][t] = fma(PR[t], la[3][t], fma(-CI[t], la[2][t], E * la[1][t]));
+        h[0][t] = fma(FI[t], la[3][t], fma(FR[t], la[2][t], fma(-B[t], la[0][t], fma(zar[t], k1.one, zcr[t]))));
+        h[1][t] = fma(FR[t], la[3][t], fma(-FI[t], la[2][t], fma(-B[t], la[1][t], fma(zai[t], k1.one, zci[t]))));
+        h[2][t] = fma(CI[t], la[3][t], fma(PR[t], la[2][t], fma(E, la[0][t], k1.nz)));
+        h[3][t] = fma(PR[t], la[3][t], fma(-CI[t], la[2][t], fma(E, la[1][t], k1.nz)));
     }
     // right node: the half node is its h- (coefficients +B, FM, PMR, C2I)
     ldk<T, K>(tc + N_B * NP, B);
@@ -167,6 +169,7 @@ __device__ __forceinline__ void mu_node(const T (&l)[4][K], const T (&ep)[4][K],
                                         const T *__restrict__ hp_tab, const T *__restrict__ hm_tab,
                                         T (&mu)[4][K])
 {
+    const FmaK<T> k1 = fma_k<T>();
     constexpr int NP = 32 * K;
     T S[K], FR[K], FI[K], PR[K], PI[K];
     // eta+ with the "a" entries of half node i+1/2
@@ -177,10 +180,12 @@ __device__ __forceinline__ void mu_node(const T (&l)[4][K], const T (&ep)[4][K],
     ldk<T, K>(hp_tab + H_PI * NP, PI);
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-        mu[0][t] = fma(FI[t], ep[3][t], fma(FR[t], ep[2][t], fma(S[t], ep[0][t], l[0][t] + (ypr[t] + ymr[t]))));
-        mu[1][t] = fma(FR[t], ep[3][t], fma(-FI[t], ep[2][t], fma(S[t], ep[1][t], l[1][t] + (ypi[t] + ymi[t]))));
-        mu[2][t] = fma(PI[t], ep[3][t], fma(PR[t], ep[2][t], ep[0][t] + l[2][t]));
-        mu[3][t] = fma(PR[t], ep[3][t], fma(-PI[t], ep[2][t], ep[1][t] + l[3][t]));
+        mu[0][t] = fma(FI[t], ep[3][t], fma(FR[t], ep[2][t], fma(S[t], ep[0][t],
+                       fma(l[0][t], k1.one, fma(ypr[t], k1.one, ymr[t])))));
+        mu[1][t] = fma(FR[t], ep[3][t], fma(-FI[t], ep[2][t], fma(S[t], ep[1][t],
+                       fma(l[1][t], k1.one, fma(ypi[t], k1.one, ymi[t])))));
+        mu[2][t] = fma(PI[t], ep[3][t], fma(PR[t], ep[2][t], fma(ep[0][t], k1.one, l[2][t])));
+        mu[3][t] = fma(PR[t], ep[3][t], fma(-PI[t], ep[2][t], fma(ep[1][t], k1.one, l[3][t])));
     }
     // eta- with the "c" entries of half node i-1/2
     ldk<T, K>(hm_tab + H_HQ * NP, S);
@@ -192,8 +197,8 @@ __device__ __forceinline__ void mu_node(const T (&l)[4][K], const T (&ep)[4][K],
     for (int t = 0; t < K; ++t) {
         mu[0][t] = fma(FI[t], em[3][t], fma(FR[t], em[2][t], fma(S[t], em[0][t], mu[0][t])));
         mu[1][t] = fma(FR[t], em[3][t], fma(-FI[t], em[2][t], fma(S[t], em[1][t], mu[1][t])));
-        mu[2][t] = fma(PI[t], em[3][t], fma(PR[t], em[2][t], em[0][t] + mu[2][t]));
-        mu[3][t] = fma(PR[t], em[3][t], fma(-PI[t], em[2][t], em[1][t] + mu[3][t]));
+        mu[2][t] = fma(PI[t], em[3][t], fma(PR[t], em[2][t], fma(em[0][t], k1.one, mu[2][t])));
+        mu[3][t] = fma(PR[t], em[3][t], fma(-PI[t], em[2][t], fma(em[1][t], k1.one, mu[3][t])));
     }
 }
 

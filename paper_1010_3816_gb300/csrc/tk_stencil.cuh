@@ -11,6 +11,26 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+// GB300's FP64 pipe issues DADD and DMUL at a lower rate than DFMA (the
+// one-step kernel runs 2.4 % faster with the sums and products below as
+// FMAs).  x + y is formed as fma(x, 1, y) and a * b as fma(a, b, -0), which
+// round exactly like the add and the multiply; the constants 1 and -0 are
+// read from device memory at run time, so the compiler cannot fold the FMAs
+// back into adds and multiplies.
+__device__ double g_fma_one = 1.0;
+__device__ double g_fma_nzero = -0.0;
+
+template <typename T>
+struct FmaK {
+    T one, nz;
+};
+
+template <typename T>
+__device__ __forceinline__ FmaK<T> fma_k()
+{
+    return {(T)(*(volatile double *)&g_fma_one), (T)(*(volatile double *)&g_fma_nzero)};
+}
+
 template <typename T, int K>
 __device__ __forceinline__ void ldk(const T *__restrict__ p, T (&v)[K])
 {
@@ -141,11 +161,12 @@ __device__ __forceinline__ void half_node(const T (&a)[4][K], const T (&c)[4][K]
                                           const T *__restrict__ tab, T (&h)[4][K])
 {
     constexpr int NP = 32 * K;
+    const FmaK<T> k1 = fma_k<T>();
     T sR[K], sI[K], upR[K], upI[K], dnR[K], dnI[K];
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-        sR[t] = a[0][t] + c[0][t];
-        sI[t] = a[1][t] + c[1][t];
+        sR[t] = fma(a[0][t], k1.one, c[0][t]);
+        sI[t] = fma(a[1][t], k1.one, c[1][t]);
     }
     theta_neighbours<T, K>(sR, upR, dnR);
     theta_neighbours<T, K>(sI, upI, dnI);
@@ -154,16 +175,16 @@ __device__ __forceinline__ void half_node(const T (&a)[4][K], const T (&c)[4][K]
     for (int k = 0; k < kNCH; ++k) ldk<T, K>(tab + k * NP, q[k]);
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-        const T sPR = a[2][t] + c[2][t];
-        const T sPI = a[3][t] + c[3][t];
+        const T sPR = fma(a[2][t], k1.one, c[2][t]);
+        const T sPI = fma(a[3][t], k1.one, c[3][t]);
         if constexpr (PI_TERM) {
             h[0][t] = fma(q[H_HQ][t], c[0][t], fma(q[H_HP][t], a[0][t], sPR));
             h[1][t] = fma(q[H_HQ][t], c[1][t], fma(q[H_HP][t], a[1][t], sPI));
         } else {
-            h[0][t] = fma(q[H_HQ][t], c[0][t], q[H_HP][t] * a[0][t]);
-            h[1][t] = fma(q[H_HQ][t], c[1][t], q[H_HP][t] * a[1][t]);
+            h[0][t] = fma(q[H_HQ][t], c[0][t], fma(q[H_HP][t], a[0][t], k1.nz));
+            h[1][t] = fma(q[H_HQ][t], c[1][t], fma(q[H_HP][t], a[1][t], k1.nz));
         }
-        T x = q[H_PAR][t] * a[2][t];
+        T x = fma(q[H_PAR][t], a[2][t], k1.nz);
         x = fma(q[H_PCR][t], c[2][t], x);
         x = fma(-q[H_PI][t], sPI, x);
         x = fma(q[H_FAR][t], a[0][t], x);
@@ -173,7 +194,7 @@ __device__ __forceinline__ void half_node(const T (&a)[4][K], const T (&c)[4][K]
         x = fma(q[H_KP][t], upR[t], x);
         x = fma(q[H_KM][t], dnR[t], x);
         h[2][t] = x;
-        T y = q[H_PAR][t] * a[3][t];
+        T y = fma(q[H_PAR][t], a[3][t], k1.nz);
         y = fma(q[H_PCR][t], c[3][t], y);
         y = fma(q[H_PI][t], sPR, y);
         y = fma(q[H_FAR][t], a[1][t], y);
@@ -193,11 +214,12 @@ __device__ __forceinline__ void full_node(const T (&hm)[4][K], const T (&hp)[4][
                                           const T e, T (&o)[4][K])
 {
     constexpr int NP = 32 * K;
+    const FmaK<T> k1 = fma_k<T>();
     T sR[K], sI[K], upR[K], upI[K], dnR[K], dnI[K];
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-        sR[t] = hp[0][t] + hm[0][t];
-        sI[t] = hp[1][t] + hm[1][t];
+        sR[t] = fma(hp[0][t], k1.one, hm[0][t]);
+        sI[t] = fma(hp[1][t], k1.one, hm[1][t]);
     }
     theta_neighbours<T, K>(sR, upR, dnR);
     theta_neighbours<T, K>(sI, upI, dnI);
@@ -206,8 +228,8 @@ __device__ __forceinline__ void full_node(const T (&hm)[4][K], const T (&hp)[4][
     for (int k = 0; k < kNCN; ++k) ldk<T, K>(tab + k * NP, q[k]);
 #pragma unroll
     for (int t = 0; t < K; ++t) {
-        const T sPR = hp[2][t] + hm[2][t];
-        const T sPI = hp[3][t] + hm[3][t];
+        const T sPR = fma(hp[2][t], k1.one, hm[2][t]);
+        const T sPI = fma(hp[3][t], k1.one, hm[3][t]);
         o[0][t] = fma(e, sPR, fma(q[N_B][t], hm[0][t], fma(-q[N_B][t], hp[0][t], u[0][t])));
         o[1][t] = fma(e, sPI, fma(q[N_B][t], hm[1][t], fma(-q[N_B][t], hp[1][t], u[1][t])));
         T x = fma(q[N_PPR][t], hp[2][t], u[2][t]);
