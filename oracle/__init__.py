@@ -90,6 +90,8 @@ def _lib():
             lib.tko_set_initial.argtypes = [C.c_void_p, _dp, _dp, _dp, _dp]
             lib.tko_get_state.restype = None
             lib.tko_get_state.argtypes = [C.c_void_p, _dp]
+            lib.tko_replace_state.restype = None
+            lib.tko_replace_state.argtypes = [C.c_void_p, _dp]
             lib.tko_add_observer.restype = C.c_int
             lib.tko_add_observer.argtypes = [C.c_void_p, C.c_double, C.c_double]
             lib.tko_run.restype = None
@@ -234,6 +236,11 @@ class Solver:
         out = np.zeros((4, self.Ntheta, self.Nr))
         _lib().tko_get_state(self._h, _ptr(out))
         return out
+
+    def replace_state(self, planes4) -> None:
+        """Overwrite the state (4 planes), keeping steps and samples."""
+        a = np.ascontiguousarray(planes4, dtype=np.float64).reshape(4, self.Ntheta, self.Nr)
+        _lib().tko_replace_state(self._h, _ptr(a))
 
     def coeffs(self):
         """(node, half) coefficient tables, each [NCOEF][Ntheta][Nr]; the half

@@ -427,6 +427,15 @@ void tko_get_state(const tko_state *S, double *out4)
     for (int k = 0; k < 4; ++k) memcpy(out4 + k * plane, S->q[k], plane * sizeof(double));
 }
 
+/* Overwrite the current state with in4 (four planes [Ntheta][Nr]), keeping the
+ * step count and the waveform samples taken so far.  Used to study the run's
+ * sensitivity to perturbations made along the way. */
+void tko_replace_state(tko_state *S, const double *in4)
+{
+    size_t plane = (size_t)S->p.Nr * S->p.Ntheta;
+    for (int k = 0; k < 4; ++k) memcpy(S->q[k], in4 + k * plane, plane * sizeof(double));
+}
+
 /* ------------------------------------------------------------------------ */
 /* The right-hand side in the square brackets of Eqs. (lw1)/(lw2):           */
 /*     (1/dr*) D (u_right - u_left) - S(u_avg)                               */

@@ -8,11 +8,15 @@ each full physical plane.  Takes about two hours on 6 cores.
 
 With --perturbed it writes kerr_25601x64_oracle_perturbed.npz instead: the same
 run from the real initial plane times 1 + 2.2e-16 * N(0, 1) (numpy's default
-generator, seed 12345), i.e. a change of about one ulp.  The difference of the
-two stored runs is the run's own conditioning, which sets the parity bar of
-the full-length test.
+generator, seed 12345), i.e. a change of about one ulp.  With --noisy it writes
+kerr_25601x64_oracle_noisy.npz: the run with every value of the state
+multiplied by 1 + 8.8e-16 * N(0, 1) after every 16th outer step (seed 12346),
+a random walk of about one ulp per outer step, the size of the rounding
+differences two correct implementations accumulate.  The differences of these
+runs from the plain one are the run's own conditioning, which sets the parity
+bar of the full-length test.
 
-    python tests/golden/make_kerr_golden.py [threads] [--perturbed]
+    python tests/golden/make_kerr_golden.py [threads] [--perturbed | --noisy]
 """
 import math
 import os
@@ -34,11 +38,14 @@ COLS = slice(0, None, 16)
 
 EPS = 2.2e-16
 SEED = 12345
+NOISE_EVERY = 16                 # outer steps between the noisy run's perturbations
+NOISE_EPS = 4 * EPS              # sqrt(16) ulps: one ulp per outer step as a random walk
 
 
 def main():
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
     perturbed = "--perturbed" in sys.argv
+    noisy = "--noisy" in sys.argv
     if args:
         oracle.set_threads(int(args[0]))
     w = KERR_25601x64
@@ -51,20 +58,31 @@ def main():
     sol.set_initial(re, im)
     t0 = time.time()
     chunk = 1200
+    rng = np.random.default_rng(SEED + 1)
     for k in range(0, w.steps, chunk):
-        sol.run(min(chunk, w.steps - k))
+        n = min(chunk, w.steps - k)
+        if noisy:
+            for _ in range(0, n, NOISE_EVERY):
+                sol.run(NOISE_EVERY)
+                st = sol.state()
+                sol.replace_state(st * (1.0 + NOISE_EPS * rng.standard_normal(st.shape)))
+        else:
+            sol.run(n)
         print(f"{k + chunk}/{w.steps} outer steps, {time.time() - t0:.0f} s", flush=True)
     st = sol.state()
     th = (np.arange(w.Ntheta) + 0.5) * (math.pi / w.Ntheta)
     wt = np.array([oracle.weight(w.s, w.m, w.variable, t) for t in th])[None, :, None]
     phys = st * wt
     np.savez_compressed(
-        os.path.join(HERE, "kerr_25601x64_oracle" + ("_perturbed" if perturbed else "") + ".npz"),
+        os.path.join(HERE, "kerr_25601x64_oracle" + ("_perturbed" if perturbed else "")
+                     + ("_noisy" if noisy else "") + ".npz"),
         wave0=sol.waveform(ids[0]), wave1=sol.waveform(ids[1]),
         state_sub=phys[:, ROWS, COLS], plane_norms=np.linalg.norm(phys.reshape(4, -1), axis=1),
         rows=np.arange(w.Ntheta)[ROWS], cols=np.arange(w.Nr)[COLS],
         note=np.array("oracle full run of " + w.name + f", {w.substeps} LW steps per outer step"
-                      + (f", real initial plane times 1 + {EPS} N(0,1), seed {SEED}" if perturbed else "")))
+                      + (f", real initial plane times 1 + {EPS} N(0,1), seed {SEED}" if perturbed else "")
+                      + (f", state times 1 + {NOISE_EPS} N(0,1) every {NOISE_EVERY} outer steps, seed "
+                         f"{SEED + 1}" if noisy else "")))
 
 
 if __name__ == "__main__":
