@@ -14,9 +14,11 @@ constexpr unsigned kFull = 0xffffffffu;
 // GB300's FP64 pipe issues DADD and DMUL at a lower rate than DFMA (the
 // one-step kernel runs 2.4 % faster with the sums and products below as
 // FMAs).  x + y is formed as fma(x, 1, y) and a * b as fma(a, b, -0), which
-// round exactly like the add and the multiply; the constants 1 and -0 are
-// read from device memory at run time, so the compiler cannot fold the FMAs
-// back into adds and multiplies.
+// round exactly like the add and the multiply; in FP64 the constants 1 and -0
+// are read from device memory (through the read-only cache) at run time, so
+// the compiler cannot fold the FMAs back into adds and multiplies.  FP32 has
+// no such gap and takes them as literals (the compiler then issues the add
+// and the multiply).
 __device__ double g_fma_one = 1.0;
 __device__ double g_fma_nzero = -0.0;
 
@@ -28,7 +30,8 @@ struct FmaK {
 template <typename T>
 __device__ __forceinline__ FmaK<T> fma_k()
 {
-    return {(T)(*(volatile double *)&g_fma_one), (T)(*(volatile double *)&g_fma_nzero)};
+    if constexpr (sizeof(T) == 8) return {__ldg(&g_fma_one), __ldg(&g_fma_nzero)};
+    else return {T(1), T(-0.0)};
 }
 
 template <typename T, int K>
