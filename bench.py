@@ -66,8 +66,11 @@ FP32_FMA_PER_CLK_PER_SM = 128
 # keyed by (workload name, precision); the capture's command and figures are in the
 # named summary under profiles/.
 MEASURED_TRAFFIC = {
-    # one launch of 100 pairs: 17.148580 + 2.553906 GB
-    ("kerr_a0.9_25601x64_38400steps", 1): ((17.148580e9 + 2.553906e9) / 100,
+    # one launch of the one-step kernel: 333.903360 + 38.050816 MB
+    ("kerr_a0.9_25601x64_38400steps", 0): (333.903360e6 + 38.050816e6,
+                                           "profiles/lw_step_f64_kerr_25601x64.md"),
+    # one launch of 100 pairs: 17.212296 + 2.561817 GB
+    ("kerr_a0.9_25601x64_38400steps", 1): ((17.212296e9 + 2.561817e9) / 100,
                                            "profiles/lw_ring_persistent_f32_kerr_25601x64.md"),
 }
 L2_FLUSH_BYTES = 256 << 20          # twice the 129 MB L2
