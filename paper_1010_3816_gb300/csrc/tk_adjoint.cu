@@ -226,6 +226,7 @@ lw_adjoint_kernel(const T *__restrict__ lam, T *__restrict__ mu_out, const T *__
     constexpr size_t SP = 4 * NP, HP = (size_t)kNCH * NP, NQ = (size_t)kNCN * NP;
     extern __shared__ __align__(16) unsigned char sh_raw[];
     T(*sh)[kAdjShared][NP] = reinterpret_cast<T(*)[kAdjShared][NP]>(sh_raw);
+    chain_start();   // lam is the previous launch's output
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     int i0, i1, left;
@@ -517,10 +518,9 @@ cudaError_t launch_adj_shape(const void *lam, void *mu, const void *half, const 
 {
     cudaError_t e = adj_smem_setup<T, K, W>();
     if (e != cudaSuccess) return e;
-    lw_adjoint_kernel<T, K, W><<<blocks, W * 32, adj_smem_bytes<T, K, W>(), st>>>(
-        (const T *)lam, (T *)mu, (const T *)half, (const T *)node, Nr, (T)(0.25 * dt_in),
-        (T)(0.5 * dt_in), inj);
-    return cudaGetLastError();
+    return launch_chained(lw_adjoint_kernel<T, K, W>, (unsigned)blocks, W * 32, adj_smem_bytes<T, K, W>(),
+                          st, (const T *)lam, (T *)mu, (const T *)half, (const T *)node, Nr,
+                          (T)(0.25 * dt_in), (T)(0.5 * dt_in), inj);
 }
 
 template <typename T, int K>

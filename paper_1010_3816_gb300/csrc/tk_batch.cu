@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(kBatchThreads)
 batch_step_kernel(const BatchMember *__restrict__ mem, int nmem, const BatchItem *__restrict__ items,
                   int nitems, int tick, int kmax, int outer, unsigned int *ctr)
 {
+    chain_start();   // the queue counters and the members' levels are the previous tick's
     const int lane = threadIdx.x & 31;
     const bool last_tick = (tick == kmax - 1);
     for (;;) {
@@ -152,12 +153,10 @@ static cudaError_t launch_batch_tick(int precision, int blocks, const BatchMembe
                                      int outer, unsigned int *ctr, cudaStream_t st)
 {
     if (precision == 0)
-        batch_step_kernel<double><<<blocks, kBatchThreads, 0, st>>>(mem, nmem, items, nitems, tick,
-                                                                    kmax, outer, ctr);
-    else
-        batch_step_kernel<float><<<blocks, kBatchThreads, 0, st>>>(mem, nmem, items, nitems, tick,
-                                                                   kmax, outer, ctr);
-    return cudaGetLastError();
+        return launch_chained(batch_step_kernel<double>, (unsigned)blocks, kBatchThreads, 0, st, mem,
+                              nmem, items, nitems, tick, kmax, outer, ctr);
+    return launch_chained(batch_step_kernel<float>, (unsigned)blocks, kBatchThreads, 0, st, mem, nmem,
+                          items, nitems, tick, kmax, outer, ctr);
 }
 
 }  // namespace tk

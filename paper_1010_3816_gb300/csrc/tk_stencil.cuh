@@ -34,6 +34,35 @@ __device__ __forceinline__ FmaK<T> fma_k()
     else return {T(1), T(-0.0)};
 }
 
+// Chained launches (programmatic dependent launch).  A kernel launched by
+// launch_chained may be scheduled while the previous kernel on the stream is
+// still running; it calls chain_start() first, which lets the next kernel be
+// scheduled in turn and then waits until the previous kernel has completed
+// and its writes are visible.  Both instructions are no-ops for a kernel
+// launched without the programmatic edge.
+__device__ __forceinline__ void chain_start()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                           cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <typename T, int K>
 __device__ __forceinline__ void ldk(const T *__restrict__ p, T (&v)[K])
 {

@@ -202,12 +202,7 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
                const T *__restrict__ node, int Nr, T eh, T en, const WaveArgs wa)
 {
     extern __shared__ __align__(16) unsigned char sh_raw[];
-    if (kUsePDL) {
-        // let the next step's launch start now; read u^n only once the
-        // previous step has completed (no-ops without a programmatic edge)
-        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-        asm volatile("griddepcontrol.wait;" ::: "memory");
-    }
+    if (kUsePDL) chain_start();
     step_sweep<T, K, W, false>(sh_raw, u_in, u_out, half, node, Nr, eh, en, wa, wa.write, 0);
     if (wa.write) advance_sample(wa);
 }
@@ -571,19 +566,9 @@ cudaError_t launch_shape(const StepLaunch &L, const WaveArgs &wa, cudaStream_t s
             (T)(0.25 * L.dt_inner), (T)(0.5 * L.dt_inner), wa);
         return cudaGetLastError();
     }
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(L.blocks);
-    cfg.blockDim = dim3(W * 32);
-    cfg.dynamicSmemBytes = step_smem_bytes<T, K, W>();
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, lw_step_kernel<T, K, W>, (const T *)L.u_in, (T *)L.u_out,
-                              (const T *)L.half, (const T *)L.node, L.Nr, (T)(0.25 * L.dt_inner),
-                              (T)(0.5 * L.dt_inner), wa);
+    return launch_chained(lw_step_kernel<T, K, W>, (unsigned)L.blocks, W * 32, step_smem_bytes<T, K, W>(),
+                          st, (const T *)L.u_in, (T *)L.u_out, (const T *)L.half, (const T *)L.node,
+                          L.Nr, (T)(0.25 * L.dt_inner), (T)(0.5 * L.dt_inner), wa);
 }
 
 template <typename T, int K, int W>
