@@ -60,8 +60,8 @@ FP64_FMA_PER_CLK_PER_SM = 2        # measured: 1.19 TFLOP/s at 1995 MHz on 152 S
 FP32_FMA_PER_CLK_PER_SM = 128
 
 
-# DRAM bytes per unit of work of the step kernel (one launch, or one pair of
-# steps of the FP32 persistent launch: dram__bytes_read.sum +
+# DRAM bytes per unit of work of the step kernel (one launch, or one sweep of
+# the FP32 persistent launch: dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the current kernel source),
 # keyed by (workload name, precision); the capture's command and figures are in the
 # named summary under profiles/.
@@ -69,10 +69,14 @@ MEASURED_TRAFFIC = {
     # one launch of the one-step kernel: 333.903360 + 38.050816 MB
     ("kerr_a0.9_25601x64_38400steps", 0): (333.903360e6 + 38.050816e6,
                                            "profiles/lw_step_f64_kerr_25601x64.md"),
-    # one launch of 100 pairs: 17.212296 + 2.561817 GB
-    ("kerr_a0.9_25601x64_38400steps", 1): ((17.212296e9 + 2.561817e9) / 100,
-                                           "profiles/lw_ring_persistent_f32_kerr_25601x64.md"),
+    # one launch of 50 sweeps of four steps: 8.739671 + 1.280446 GB
+    ("kerr_a0.9_25601x64_38400steps", 1): ((8.739671e9 + 1.280446e9) / 50,
+                                           "profiles/lw_multi_persistent_f32_kerr_25601x64.md"),
 }
+# FP32 on the Kerr workload: every inner step of the solve in one cooperative
+# launch, four Lax-Wendroff steps per sweep over the grid (25601 columns: at
+# least 4 per warp of 8 warps on each of the 152 SMs).
+FP32_STEPS_PER_SWEEP = 4
 L2_FLUSH_BYTES = 256 << 20          # twice the 129 MB L2
 
 
@@ -555,12 +559,19 @@ def main() -> int:
         solver.precompute(w.a, w.M, w.s, w.m)
         w = w.with_(substeps=solver.substeps)
     updates = w.points * n_outer * w.substeps
-    # the library's default: FP32 runs the solve's inner steps as pairs in one
-    # persistent launch (plus one single step if their number is odd); FP64
-    # launches one step at a time on this grid
-    spl = 2 if args.precision == 1 else 1
+    # the library's default: FP32 runs the solve's inner steps as sweeps of
+    # four in one persistent launch (whole outer steps), the rest as pairs in
+    # a second one and an odd last step alone; FP64 launches one step at a
+    # time on this grid
+    spl = FP32_STEPS_PER_SWEEP if args.precision == 1 else 1
     inner_steps = n_outer * w.substeps
-    step_launches = (1 + inner_steps % 2) if args.precision == 1 else inner_steps
+    if args.precision == 1:
+        unit = w.substeps // math.gcd(spl, w.substeps)
+        sweeps = inner_steps // spl // unit * unit
+        rest = inner_steps - sweeps * spl
+        step_launches = int(sweeps > 0) + int(rest >= 2) + rest % 2
+    else:
+        step_launches = inner_steps
     launches_per_solve = 3 + step_launches + len(w.observers)
     re, im = initial_planes(w)
     d_re = torch.from_numpy(re).cuda()
@@ -631,18 +642,19 @@ def main() -> int:
                 (NUM_SMS * FP64_FMA_PER_CLK_PER_SM * f_clk),
                 "launch_us": kern_s * 1e6}
     else:
-        # the unit of work is a pair of inner steps: it reads u^n and the
-        # tables once and writes u^{n+2}; algorithmic bytes per pair =
-        # (32 + 84) B per point.  All pairs of the solve run in one launch.
-        pair_s = spl * kern_s
+        # the unit of work is one sweep of FP32_STEPS_PER_SWEEP inner steps: it
+        # reads u^n and the tables once and writes u^{n+4}; algorithmic bytes
+        # per sweep = (32 + 84) B per point.  All sweeps of the solve run in
+        # one launch.
+        sweep_s = spl * kern_s
         alg = (STATE_BYTES_PER_UPDATE[1] + TABLE_BYTES_PER_UPDATE[1]) * pts
-        achieved = alg / pair_s / 1e9
+        achieved = alg / sweep_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": 6794.1, "unit": "GB/s",
                 "frac": achieved / 6794.1, "traffic": traffic,
-                "kernel": "lw_ring_persistent_kernel<float>",
-                "algorithmic_bytes_per_pair": alg, "inner_steps_per_pair": spl,
+                "kernel": "lw_multi_persistent_kernel<float>",
+                "algorithmic_bytes_per_sweep": alg, "inner_steps_per_sweep": spl,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
-                "traffic_source": traffic_src, "pair_us": pair_s * 1e6}
+                "traffic_source": traffic_src, "sweep_us": sweep_s * 1e6}
     sb = STATE_BYTES_PER_UPDATE[args.precision] * pts / kern_s / 1e9
     tb = TABLE_BYTES_PER_UPDATE[args.precision] * pts / kern_s / 1e9
     roof_hbm = {"bound": "hbm", "achieved": sb, "peak": 6794.1, "unit": "GB/s",

@@ -236,8 +236,11 @@ tk_status tk_stability_bound(tk_solver *S, double growth_per_step, double *dt_ma
                              int *substeps_needed);
 
 /* Lax-Wendroff steps per kernel launch: 1, 2, -1 (every inner step of a
- * tk_step call in one persistent launch: single steps for TK_PREC_F64, pairs
- * for TK_PREC_F32), or 0 for the default: -1 for TK_PREC_F32, whose step is
+ * tk_step call in one persistent launch: single steps for TK_PREC_F64; for
+ * TK_PREC_F32 sweeps of four steps over the grid where it has at least four
+ * columns per warp of one block per SM -- the sweeps cover whole outer steps
+ * -- and pairs of steps, in a second launch, for the rest, with an odd last
+ * step launched alone), or 0 for the default: -1 for TK_PREC_F32, whose step is
  * bound by memory traffic; for TK_PREC_F64, whose step is bound by FP64
  * arithmetic, 1, or -1 on grids too small for one block per SM (where launch
  * overhead and latency dominate).  With 2,

@@ -209,6 +209,7 @@ tk_status tk_make_grid(tk_solver **out, double rstar_min, double rstar_max, int 
     S->persist_blocks = (precision == TK_PREC_F32)
                             ? S->fused_blocks
                             : tk::persistent_grid_blocks(precision, S->K, Nr, S->num_sms, S->warps);
+    S->multi_blocks = tk::multi_grid_shape(precision, S->K, Nr, S->num_sms, &S->multi_warps);
     set_launch_mode(S, 0);
 
     const size_t se = state_elems(S);
@@ -498,12 +499,13 @@ tk_status tk_step(tk_solver *S, int n)
     if (S->persist && (long long)n * S->substeps >= 2) {
         // every inner step of the call in one cooperative launch; its waits
         // are bounded, and a wait that timed out is reported here
-        const size_t fbytes = (size_t)S->persist_blocks * sizeof(unsigned int) + sizeof(int);
+        const int nflags = S->persist_blocks > S->multi_blocks ? S->persist_blocks : S->multi_blocks;
+        const size_t fbytes = (size_t)nflags * sizeof(unsigned int) + sizeof(int);
         if (!S->pflags) {
             st = alloc(S, (void **)&S->pflags, fbytes);
             if (st != TK_OK) return st;
         }
-        int *perr = (int *)(S->pflags + S->persist_blocks);
+        int *perr = (int *)(S->pflags + nflags);
         TK_CUDA(S, cudaMemsetAsync(S->pflags, 0, fbytes, S->stream));
         tk::StepLaunch L;
         tkh::fill_launch(S, L);
@@ -514,12 +516,39 @@ tk_status tk_step(tk_solver *S, int n)
         const long long inner = (long long)n * S->substeps;
         if (inner > 0x7fffffff) return fail(S, TK_ERR_ARG, "tk_step: %d outer steps are too many for one call", n);
         if (S->precision == TK_PREC_F32) {
-            // pairs of steps in one launch; an odd last step by the one-step kernel
-            const long long pairs = inner / 2;
-            TK_CUDA(S, tk::launch_ring_persistent(L, S->u[S->cur ^ 1], (int)pairs, S->substeps, S->pflags,
-                                                  perr, S->stream));
-            if (pairs & 1) S->cur ^= 1;
-            if (inner & 1) {
+            // groups of tk::multi_levels() steps per sweep in one launch (large
+            // grids), ending on an outer step's boundary; the rest as pairs of
+            // steps in one launch and an odd last step by the one-step kernel
+            long long rem = inner;
+            if (S->multi_blocks > 0) {
+                const int lv = tk::multi_levels();
+                long long unit = S->substeps;   // groups per run of whole outer steps
+                for (int d = lv; d > 1; --d)
+                    if (lv % d == 0 && unit % d == 0) {
+                        unit /= d;
+                        break;
+                    }
+                const long long groups = rem / lv / unit * unit;
+                if (groups > 0) {
+                    tk::StepLaunch LM = L;
+                    LM.blocks = S->multi_blocks;
+                    LM.warps = S->multi_warps;
+                    TK_CUDA(S, tk::launch_multi_persistent(LM, S->u[S->cur ^ 1], (int)groups, S->substeps,
+                                                           S->pflags, perr, S->stream));
+                    if (groups & 1) S->cur ^= 1;
+                    rem -= groups * lv;
+                    L.u_in = S->u[S->cur];
+                    // the flags count again from zero; the error flag is kept
+                    TK_CUDA(S, cudaMemsetAsync(S->pflags, 0, (size_t)nflags * sizeof(unsigned int), S->stream));
+                }
+            }
+            const long long pairs = rem / 2;
+            if (pairs > 0) {
+                TK_CUDA(S, tk::launch_ring_persistent(L, S->u[S->cur ^ 1], (int)pairs, S->substeps, S->pflags,
+                                                      perr, S->stream));
+                if (pairs & 1) S->cur ^= 1;
+            }
+            if (rem & 1) {
                 tk::StepLaunch L1;
                 tkh::fill_launch(S, L1);
                 L1.u_in = S->u[S->cur];

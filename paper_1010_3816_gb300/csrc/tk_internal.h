@@ -125,6 +125,13 @@ cudaError_t launch_ring_persistent(const StepLaunch &L, void *u_other, int n_pai
                                    unsigned int *flags, int *err, cudaStream_t st);
 // Launch shape of the two-step kernel.
 int fused_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
+// FP32, large grids: groups of multi_levels() steps per sweep in one
+// cooperative launch (one block per SM); 0 blocks where it does not apply.
+// The call must start on an outer step's boundary.
+int multi_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
+int multi_levels();
+cudaError_t launch_multi_persistent(const StepLaunch &L, void *u_other, int n_groups, int k,
+                                    unsigned int *flags, int *err, cudaStream_t st);
 // Launch shape of the adjoint step kernel: returns the number of blocks and
 // sets *warps to the warps per block.
 int adjoint_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);

@@ -52,6 +52,8 @@ struct tk_solver {
     int persist = 0;            // 1: all inner steps of a tk_step call in one persistent launch
     int persist_blocks = 0;     // its grid (0: the grid is too large for it)
     unsigned int *pflags = nullptr;     // its per-block step flags, then the error flag
+    int multi_blocks = 0;       // FP32: groups of tk::multi_levels() steps per sweep (0: not used)
+    int multi_warps = 4;
     int fuse = 0;               // 1: inner steps in pairs, one two-step launch per pair
     int fuse_mode = 0;          // as set by tk_set_steps_per_launch (0: automatic)
     int fused_blocks = 1;       // two-step kernel launch shape

@@ -539,6 +539,139 @@ lw_ring_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__r
     if (wa.write) advance_sample(wa, (2 * n_pairs) / k);
 }
 
+// LV Lax-Wendroff steps per sweep, u^n -> u^{n+LV} (the FP32 default on
+// large grids with every step of a call in one launch): the state and the
+// tables cross DRAM once per LV steps.  The ring sweep above generalised: a
+// warp owns the output columns [i0, i1) and computes level l (1..LV) on
+// [i0 - (LV - l), i1 + (LV - l)), recomputing the halo; at sweep position p
+// (the newest level-0 column) level l forms the half node between columns
+// p - l and p - l + 1 and the node p - l, from level l - 1's values at those
+// columns (the one formed at this position and the one kept from the last).
+// Column c's tables are used by level 1 at position c + 1 and by level LV at
+// c + LV, so the ring holds LV + 1 columns: LV in use and one in flight.
+// Every node and half node does the one-step kernel's arithmetic on the same
+// operands (bit-identical to LV single steps).  mask bit l - 1: an outer step
+// ends after level l; off[l - 1]: its sample after the counter's value.
+constexpr int kSweepLevels = 4;
+
+template <typename T, int K>
+constexpr int multi_warps()
+{
+    return K == 1 ? 16 : K == 2 ? 8 : 4;
+}
+
+template <typename T, int K, int W, int LV>
+constexpr size_t multi_smem_bytes()
+{
+    return (size_t)W * (LV + 1) * kSlotCols * 32 * K * sizeof(T);
+}
+
+template <typename T, int K, int W, int LV>
+__device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, const T *__restrict__ u_in,
+                                            T *__restrict__ u_out, const T *__restrict__ half,
+                                            const T *__restrict__ node, int Nr, T en,
+                                            const WaveArgs &wa, int mask, const int (&off)[LV])
+{
+    constexpr int NP = 32 * K;
+    constexpr int S = LV + 1;
+    constexpr size_t SP = 4 * NP;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    T *ring = reinterpret_cast<T *>(sh_raw) + (size_t)wib * S * kSlotCols * NP;
+    int i0, i1, left;
+    warp_range<W>(Nr, wib, &i0, &i1, &left);
+    const int row = lane * K;
+    if (i1 <= i0) return;
+    T hm[LV][4][K];   // level l + 1: the half node formed at the last position
+    T um[LV][4][K];   // level l: the value formed at the last position
+#pragma unroll
+    for (int l = 0; l < LV; ++l) {
+        zero_col<T, K>(hm[l]);
+        zero_col<T, K>(um[l]);
+    }
+    const int pa = i0 - LV, pb = i1 + LV - 1;
+    ring_fetch<T, K>(ring, half, node, pa, Nr, row);
+    T cn[4][K];
+    if (pa >= 0) load_state<T, K, true>(u_in + (size_t)pa * SP + row, cn);
+    else zero_col<T, K>(cn);
+    int cur = 0;
+    for (int p = pa; p <= pb; ++p) {
+        const int nxt = cur == S - 1 ? 0 : cur + 1;
+        if (p + 1 <= pb)
+            ring_fetch<T, K>(ring + nxt * kSlotCols * NP, half, node, p + 1, Nr, row);
+        else
+            cp_async_commit();
+        cp_async_wait_one();
+        T cu[4][K];   // level l - 1 at column p - l + 1
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int t = 0; t < K; ++t) cu[c][t] = cn[c][t];
+        if (p + 1 <= pb && p + 1 < Nr)
+            load_state<T, K, true>(u_in + (size_t)(p + 1) * SP + row, cn);
+        else
+            zero_col<T, K>(cn);
+#pragma unroll
+        for (int l = 1; l <= LV; ++l) {
+            const int c = p - l;
+            int sl = cur - (l - 1);
+            if (sl < 0) sl += S;
+            const T *tab = ring + sl * kSlotCols * NP;   // tables of column c
+            T hp[4][K], uc[4][K];
+            if (c >= i0 - (LV - l) - 1 && c >= 0 && c + 1 < Nr)
+                half_node<T, K>(um[l - 1], cu, tab + row, hp);
+            else
+                zero_col<T, K>(hp);
+            if (c >= i0 - (LV - l) && c >= 1 && c <= Nr - 2)
+                full_node<T, K>(hm[l - 1], hp, um[l - 1], tab + kSlotNode * NP + row, en, uc);
+            else
+                zero_col<T, K>(uc);
+            if (l == LV && c >= i0) store_col<T, K>(u_out + (size_t)c * SP + row, uc);
+            if (((mask >> (l - 1)) & 1) && c >= i0 && c < i1)
+                observe<T, K>(c, lane, uc, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, off[l - 1]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    um[l - 1][q][t] = cu[q][t];
+                    hm[l - 1][q][t] = hp[q][t];
+                    cu[q][t] = uc[q][t];
+                }
+        }
+        cur = nxt;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Groups of LV steps in one cooperative launch, the blocks waiting for their
+// two neighbours between groups (each block owns at least LV columns, so the
+// columns a group reads beyond a block's range belong to its neighbours).
+// Group g takes inner steps LV g .. LV g + LV - 1 of the call, which starts on
+// an outer step's boundary (k inner steps per outer step).
+template <typename T, int K, int W, int LV>
+__global__ void __launch_bounds__(W * 32, 1)
+lw_multi_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__restrict__ node,
+                           int Nr, T en, const WaveArgs wa, int n_groups, int k, unsigned int *flags,
+                           int *err)
+{
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    for (int g = 0; g < n_groups; ++g) {
+        const T *in = (g & 1) ? u1 : u0;
+        T *out = (g & 1) ? u0 : u1;
+        const int t = LV * g;
+        int mask = 0;
+        int off[LV];
+#pragma unroll
+        for (int l = 0; l < LV; ++l) {
+            if (wa.write && (t + l + 1) % k == 0) mask |= 1 << l;
+            off[l] = (t + l + 1) / k - 1;
+        }
+        multi_sweep<T, K, W, LV>(sh_raw, in, out, half, node, Nr, en, wa, mask, off);
+        if (g + 1 < n_groups && !neighbour_barrier(flags, (unsigned)(g + 1), err)) break;
+    }
+    if (wa.write) advance_sample(wa, (LV * n_groups) / k);
+}
+
 template <typename T, int K, int W>
 constexpr size_t step_smem_bytes()
 {
@@ -802,6 +935,58 @@ cudaError_t launch_ring_persistent(const StepLaunch &L, void *u_other, int n_pai
     if (L.K == 1) return launch_ring_persistent_typed<float, 1>(L, u_other, n_pairs, k, flags, err, st);
     if (L.K == 2) return launch_ring_persistent_typed<float, 2>(L, u_other, n_pairs, k, flags, err, st);
     return launch_ring_persistent_typed<float, 4>(L, u_other, n_pairs, k, flags, err, st);
+}
+
+namespace {
+
+template <typename T, int K, int W>
+cudaError_t launch_multi_persistent_w(const StepLaunch &L, void *u_other, int n_groups, int k,
+                                      unsigned int *flags, int *err, cudaStream_t st)
+{
+    constexpr size_t smem = multi_smem_bytes<T, K, W, kSweepLevels>();
+    static cudaError_t e0 = cudaFuncSetAttribute(lw_multi_persistent_kernel<T, K, W, kSweepLevels>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e0 != cudaSuccess) return e0;
+    WaveArgs wa;
+    wa.write = L.write_wave;
+    wa.sample = L.sample_ctr;
+    wa.done = L.done_ctr;
+    wa.cap = L.wave_cap;
+    wa.wave = L.wave;
+    wa.w_row = L.w_row;
+    wa.obs = L.obs;
+    T *u0 = (T *)L.u_in, *u1 = (T *)u_other;
+    const T *half = (const T *)L.half, *node = (const T *)L.node;
+    int Nr = L.Nr;
+    T en = (T)(0.5 * L.dt_inner);
+    void *args[] = {&u0, &u1, &half, &node, &Nr, &en, &wa, &n_groups, &k, &flags, &err};
+    return cudaLaunchCooperativeKernel((const void *)lw_multi_persistent_kernel<T, K, W, kSweepLevels>,
+                                       dim3(L.blocks), dim3(W * 32), args, smem, st);
+}
+
+}  // namespace
+
+int multi_grid_shape(int precision, int K, int Nr, int num_sms, int *warps)
+{
+    const int W = K == 1 ? multi_warps<float, 1>() : K == 2 ? multi_warps<float, 2>() : multi_warps<float, 4>();
+    *warps = W;
+    if (precision != 1 || (long long)Nr < (long long)num_sms * W * kSweepLevels) return 0;
+    return num_sms;
+}
+
+int multi_levels() { return kSweepLevels; }
+
+cudaError_t launch_multi_persistent(const StepLaunch &L, void *u_other, int n_groups, int k,
+                                    unsigned int *flags, int *err, cudaStream_t st)
+{
+    if (L.precision != 1) return cudaErrorInvalidValue;
+    if (L.K == 1 && L.warps == multi_warps<float, 1>())
+        return launch_multi_persistent_w<float, 1, multi_warps<float, 1>()>(L, u_other, n_groups, k, flags, err, st);
+    if (L.K == 2 && L.warps == multi_warps<float, 2>())
+        return launch_multi_persistent_w<float, 2, multi_warps<float, 2>()>(L, u_other, n_groups, k, flags, err, st);
+    if (L.K == 4 && L.warps == multi_warps<float, 4>())
+        return launch_multi_persistent_w<float, 4, multi_warps<float, 4>()>(L, u_other, n_groups, k, flags, err, st);
+    return cudaErrorInvalidValue;
 }
 
 int persistent_grid_blocks(int precision, int K, int Nr, int num_sms, int warps)

@@ -111,6 +111,14 @@ PERSISTENT_CASES = [
     (1, _grid(3001, 64, substeps=3), (5,)),                 # FP32, an odd last step
     (1, _grid(5003, 32, substeps=1), (9,)),                 # FP32 K = 1
     (1, _grid(1301, 128, substeps=4), (3,)),                # FP32 K = 4
+    # FP32 grids with at least 4 columns per warp of one block per SM: sweeps
+    # of four steps, ending on outer step boundaries; the rest as pairs and a
+    # single step
+    (1, _grid(4901, 64, substeps=2), (7, 1, 4)),            # K = 2: 3 sweeps + 1 pair; a pair; 2 sweeps
+    (1, _grid(4901, 64, substeps=3), (5, 4)),               # k = 3: 3 sweeps + a pair + a single step
+    (1, _grid(9800, 32, substeps=1), (9, 2)),               # K = 1: 2 sweeps + a single step
+    (1, _grid(2500, 128, substeps=4), (3, 1)),              # K = 4: 3 sweeps; 1 sweep
+    (1, _grid(5000, 64, substeps=8), (2, 3)),               # k = 8: 4 sweeps; 6 sweeps
 ]
 
 
@@ -118,8 +126,9 @@ PERSISTENT_CASES = [
                          ids=[f"case{k}" for k in range(len(PERSISTENT_CASES))])
 def test_persistent_launch_bit_identical(precision, w, calls):
     """All inner steps of each tk_step call in one cooperative launch (FP64:
-    single steps; FP32: pairs of steps), blocks waiting on their neighbours in
-    between: the same bits as one launch per step, waveforms included."""
+    single steps; FP32: sweeps of four steps on large grids, then pairs of
+    steps), blocks waiting on their neighbours in between: the same bits as
+    one launch per step, waveforms included."""
     s1, w1 = _run(w, precision, 1, calls)
     sp, wp = _run(w, precision, -1, calls)
     assert np.isfinite(s1).all()
