@@ -136,14 +136,14 @@ using tkh::fail;
 constexpr double kAutoGrowthPerStep = 2.5e-5;
 
 // Launch structure for tk_step.  mode 0 (automatic): FP32, bound by memory,
-// runs every step of a call as pairs of steps in one persistent launch (two
-// steps per read of the state and the tables, and no per-launch tail: a
-// block waits only for its neighbours, so random differences in block speed
-// average out); FP64, bound by its arithmetic (which the two-step kernel's
+// runs every step of a call in one persistent launch, as sweeps of four steps
+// on large grids and pairs of steps otherwise (four or two steps per read of
+// the state and the tables, and no per-launch tail: a block waits only for
+// its neighbours, so random differences in block speed average out); FP64, bound by its arithmetic (which the two-step kernel's
 // overlap adds to), takes one step per launch, and every step of a call in
 // one persistent launch on grids too small for one block per SM (where
-// launch overhead and latency dominate).  Measured: FP32 25601 x 64, 16.5
-// against 18.3 us per step with a launch per pair; FP64 1601 x 32, 9.1
+// launch overhead and latency dominate).  Measured: FP32 25601 x 64, 15.7 us
+// per step in sweeps of four, 16.6 in pairs, 18.3 with a launch per pair; FP64 1601 x 32, 9.1
 // against 9.7 us; FP64 25601 x 64, 155.3 against 155.5 us (not worth the
 // host synchronization the persistent launch needs).
 static void set_launch_mode(tk_solver *S, int mode)
