@@ -32,7 +32,7 @@ EXPORTS = ("tk_make_grid", "tk_precompute_coeffs", "tk_set_initial_data", "tk_ad
            "tk_batch_create", "tk_batch_step", "tk_batch_tune", "tk_batch_set_segment",
            "tk_batch_set_graph_chunk", "tk_batch_info", "tk_batch_last_error", "tk_batch_destroy",
            "tk_extract_noalloc", "tk_adjoint", "tk_set_initial_gaussian", "tk_get_substeps",
-           "tk_set_steps_per_launch", "tk_param_gradient")
+           "tk_set_steps_per_launch", "tk_param_gradient", "tk_check_bounded_wait")
 
 
 class TkError(RuntimeError):
@@ -89,6 +89,7 @@ def load_library(path: str = LIB_PATH):
             "tk_set_steps_per_launch": (C.c_int, [_vp, C.c_int]),
             "tk_param_gradient": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_int,
                                             C.POINTER(C.c_double)]),
+            "tk_check_bounded_wait": (C.c_int, [C.c_int, C.c_int, C.c_int64, _ip]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -245,6 +246,15 @@ def tk_param_gradient(h, param: int, dL_dwave, checkpoint_every: int = 0) -> flo
     _check(h, load_library().tk_param_gradient(h, int(param), p, dev, int(checkpoint_every),
                                                C.byref(g)))
     return g.value
+
+
+def tk_check_bounded_wait(n_blocks: int, silent: int, max_polls: int = 1 << 24) -> bool:
+    """Run the persistent launches' neighbour wait with block `silent` never
+    publishing; True if the waits ran out and raised the error flag."""
+    t = C.c_int(0)
+    _check(None, load_library().tk_check_bounded_wait(int(n_blocks), int(silent), int(max_polls),
+                                                      C.byref(t)))
+    return bool(t.value)
 
 
 def tk_steps_done(h) -> int:

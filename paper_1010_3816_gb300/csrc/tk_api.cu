@@ -734,6 +734,29 @@ tk_status tk_synchronize(tk_solver *S)
     return TK_OK;
 }
 
+tk_status tk_check_bounded_wait(int n_blocks, int silent, int64_t max_polls, int *timed_out)
+{
+    if (n_blocks < 2 || n_blocks > 64 || silent < -1 || silent >= n_blocks || max_polls < 1 || !timed_out) {
+        snprintf(g_err, sizeof g_err, "tk_check_bounded_wait: bad arguments");
+        return TK_ERR_ARG;
+    }
+    unsigned int *flags = nullptr;
+    const size_t bytes = (size_t)n_blocks * sizeof(unsigned int) + sizeof(int);
+    cudaError_t e = cudaMalloc((void **)&flags, bytes);
+    if (e == cudaSuccess) e = cudaMemset(flags, 0, bytes);
+    int *err = (int *)(flags + n_blocks);
+    if (e == cudaSuccess) e = tk::launch_wait_check(n_blocks, silent, (long long)max_polls, flags, err, 0);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (flags) cudaFree(flags);
+    if (e != cudaSuccess) {
+        snprintf(g_err, sizeof g_err, "tk_check_bounded_wait: %s", cudaGetErrorString(e));
+        return TK_ERR_CUDA;
+    }
+    *timed_out = h != 0;
+    return TK_OK;
+}
+
 const char *tk_last_error(const tk_solver *S) { return S ? S->err : g_err; }
 
 void tk_destroy(tk_solver *S)

@@ -117,6 +117,10 @@ int step_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
 // second level; flags: one zeroed unsigned int per block; *err set on a wait
 // that timed out).
 int persistent_grid_blocks(int precision, int K, int Nr, int num_sms, int warps);
+// Diagnostic of the persistent launches' bounded neighbour wait (one-warp
+// blocks; flags: n_blocks zeroed unsigned ints).
+cudaError_t launch_wait_check(int n_blocks, int silent, long long max_spins, unsigned int *flags,
+                              int *err, cudaStream_t st);
 cudaError_t launch_lw_persistent(const StepLaunch &L, void *u_other, int n_inner, int substeps,
                                  unsigned int *flags, int *err, cudaStream_t st);
 // Pairs of steps in one cooperative launch (FP32, the two-step kernel's grid

@@ -226,7 +226,8 @@ __device__ __forceinline__ unsigned int load_acquire(const unsigned int *p)
     return v;
 }
 
-__device__ __forceinline__ bool neighbour_barrier(unsigned int *flags, unsigned int epoch, int *err)
+__device__ __forceinline__ bool neighbour_barrier(unsigned int *flags, unsigned int epoch, int *err,
+                                                  long long max_spins = kMaxSpins)
 {
     __shared__ int ok;
     __syncthreads();                       // the block's stores of this step are issued
@@ -239,7 +240,7 @@ __device__ __forceinline__ bool neighbour_barrier(unsigned int *flags, unsigned 
             if (nb < 0 || nb >= (int)gridDim.x) continue;
             long long spins = 0;
             while (load_acquire(&flags[nb]) < epoch) {
-                if (++spins > kMaxSpins || *(volatile int *)err) {
+                if (++spins > max_spins || *(volatile int *)err) {
                     good = 0;
                     break;
                 }
@@ -269,6 +270,16 @@ lw_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__restri
         if (s + 1 < n_inner && !neighbour_barrier(flags, (unsigned)(s + 1), err)) break;
     }
     if (wa.write) advance_sample(wa, n_inner / substeps);
+}
+
+// Diagnostic of the bounded wait: every block but `silent` publishes epoch 1
+// and waits for its neighbours as the persistent kernels do between steps;
+// `silent` returns at once, so its neighbours' waits run out after max_spins
+// polls and set *err.
+__global__ void wait_check_kernel(unsigned int *flags, int *err, int silent, long long max_spins)
+{
+    if ((int)blockIdx.x == silent) return;
+    neighbour_barrier(flags, 1u, err, max_spins);
 }
 
 // Two Lax-Wendroff steps per launch, u^n -> u^{n+2}, for the HBM-bound
@@ -998,6 +1009,14 @@ int persistent_grid_blocks(int precision, int K, int Nr, int num_sms, int warps)
     return K == 1 ? persistent_blocks<float, 1>(Nr, num_sms, warps)
          : K == 2 ? persistent_blocks<float, 2>(Nr, num_sms, warps)
                   : persistent_blocks<float, 4>(Nr, num_sms, warps);
+}
+
+cudaError_t launch_wait_check(int n_blocks, int silent, long long max_spins, unsigned int *flags,
+                              int *err, cudaStream_t st)
+{
+    void *args[] = {&flags, &err, &silent, &max_spins};
+    return cudaLaunchCooperativeKernel((const void *)wait_check_kernel, dim3(n_blocks), dim3(32), args,
+                                       0, st);
 }
 
 cudaError_t launch_lw_persistent(const StepLaunch &L, void *u_other, int n_inner, int substeps,
