@@ -66,11 +66,11 @@ FP32_FMA_PER_CLK_PER_SM = 128
 # keyed by (workload name, precision); the capture's command and figures are in the
 # named summary under profiles/.
 MEASURED_TRAFFIC = {
-    # one launch of the one-step kernel: 333.903360 + 38.050816 MB
-    ("kerr_a0.9_25601x64_38400steps", 0): (333.903360e6 + 38.050816e6,
+    # one launch of the one-step kernel: 333.910272 + 37.338880 MB
+    ("kerr_a0.9_25601x64_38400steps", 0): (333.910272e6 + 37.338880e6,
                                            "profiles/lw_step_f64_kerr_25601x64.md"),
-    # one launch of 50 sweeps of four steps: 8.739671 + 1.280446 GB
-    ("kerr_a0.9_25601x64_38400steps", 1): ((8.739671e9 + 1.280446e9) / 50,
+    # one launch of 50 sweeps of four steps: 8.633103 + 1.269226 GB
+    ("kerr_a0.9_25601x64_38400steps", 1): ((8.633103104e9 + 1.269225728e9) / 50,
                                            "profiles/lw_multi_persistent_f32_kerr_25601x64.md"),
 }
 # FP32 on the Kerr workload: every inner step of the solve in one cooperative

@@ -46,7 +46,8 @@ void release(tk_solver *S)
 {
     void *ptrs[] = {S->u[0], S->u[1], S->half, S->node, S->b_node, S->w_row,
                     S->x_node, S->x_half, S->ang, S->staging, S->flag, S->stiff, S->ctr, S->wave,
-                    S->adj[0], S->adj[1], S->u_init, S->dhalf, S->dnode, S->db_node, S->pflags};
+                    S->adj[0], S->adj[1], S->u_init, S->dhalf, S->dnode, S->db_node, S->pflags,
+                    S->obs_scr};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < 2; ++k)
@@ -520,7 +521,10 @@ tk_status tk_step(tk_solver *S, int n)
             // grids), ending on an outer step's boundary; the rest as pairs of
             // steps in one launch and an odd last step by the one-step kernel
             long long rem = inner;
-            if (S->multi_blocks > 0) {
+            int obs_i0[tk::kMaxObservers];
+            for (int o = 0; o < S->nobs; ++o) obs_i0[o] = S->obs[o].i0;
+            if (S->multi_blocks > 0 &&
+                tk::multi_obs_fit(S->Nr, S->multi_blocks, S->multi_warps, obs_i0, S->nobs)) {
                 const int lv = tk::multi_levels();
                 long long unit = S->substeps;   // groups per run of whole outer steps
                 for (int d = lv; d > 1; --d)
@@ -529,12 +533,16 @@ tk_status tk_step(tk_solver *S, int n)
                         break;
                     }
                 const long long groups = rem / lv / unit * unit;
+                if (groups > 0 && !S->obs_scr) {
+                    st = alloc(S, &S->obs_scr, tk::multi_obs_scratch_bytes(S->K, S->multi_blocks, S->multi_warps));
+                    if (st != TK_OK) return st;
+                }
                 if (groups > 0) {
                     tk::StepLaunch LM = L;
                     LM.blocks = S->multi_blocks;
                     LM.warps = S->multi_warps;
                     TK_CUDA(S, tk::launch_multi_persistent(LM, S->u[S->cur ^ 1], (int)groups, S->substeps,
-                                                           S->pflags, perr, S->stream));
+                                                           S->pflags, perr, S->obs_scr, S->stream));
                     if (groups & 1) S->cur ^= 1;
                     rem -= groups * lv;
                     L.u_in = S->u[S->cur];

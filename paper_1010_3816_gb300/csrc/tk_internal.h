@@ -134,8 +134,13 @@ int fused_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
 // The call must start on an outer step's boundary.
 int multi_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);
 int multi_levels();
+// scratch: multi_obs_scratch_bytes(K, blocks, warps) of device memory for the
+// waveform samples; the sweep applies only if multi_obs_fit (no warp holds
+// more than four distinct observer columns).
+size_t multi_obs_scratch_bytes(int K, int blocks, int warps);
+bool multi_obs_fit(int Nr, int blocks, int warps, const int *obs_i0, int nobs);
 cudaError_t launch_multi_persistent(const StepLaunch &L, void *u_other, int n_groups, int k,
-                                    unsigned int *flags, int *err, cudaStream_t st);
+                                    unsigned int *flags, int *err, void *scratch, cudaStream_t st);
 // Launch shape of the adjoint step kernel: returns the number of blocks and
 // sets *warps to the warps per block.
 int adjoint_grid_shape(int precision, int K, int Nr, int num_sms, int *warps);

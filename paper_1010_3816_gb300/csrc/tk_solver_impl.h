@@ -52,6 +52,7 @@ struct tk_solver {
     int persist = 0;            // 1: all inner steps of a tk_step call in one persistent launch
     int persist_blocks = 0;     // its grid (0: the grid is too large for it)
     unsigned int *pflags = nullptr;     // its per-block step flags, then the error flag
+    void *obs_scr = nullptr;    // the four-step sweep's waveform-sample scratch
     int multi_blocks = 0;       // FP32: groups of tk::multi_levels() steps per sweep (0: not used)
     int multi_warps = 4;
     int fuse = 0;               // 1: inner steps in pairs, one two-step launch per pair

@@ -290,6 +290,50 @@ __device__ __forceinline__ void full_node(const T (&hm)[4][K], const T (&hp)[4][
 // Partial bilinear sample (Sec. "waveform extraction" of the design notes):
 // slot 0 holds (1 - fr) * [(1-fth) w_j0 Phi_{i0,j0} + fth w_j0+1 Phi_{i0,j0+1}],
 // slot 1 the same at column i0 + 1 times fr; the sample is slot 0 + slot 1.
+// observe_one: observer k's slot from the column's Phi_R, Phi_I (K rows per
+// lane); all 32 lanes take part, lane 0 writes.
+template <typename T, int K>
+__device__ __forceinline__ void observe_one(int lane, int k, int slot, const T (&re)[K], const T (&im)[K],
+                                            const ObsDev &obs, double *wave, int64_t cap,
+                                            const long long *sample_ctr, const double *w_row,
+                                            int sample_offset)
+{
+    // only rows j0 and j0 + 1 contribute: fetch them from the lanes that hold
+    // them (two shuffles) and let lane 0 do the few FP64 operations, instead
+    // of a reduction over the warp, whose FP64 adds hold GB300's FP64 pipe for
+    // microseconds
+    const int j0 = obs.j0[k];
+    const int t0 = j0 % K, t1 = (j0 + 1) % K;
+    T ar = re[0], ai = im[0], br = re[0], bi = im[0];
+#pragma unroll
+    for (int t = 1; t < K; ++t) {
+        if (t == t0) {
+            ar = re[t];
+            ai = im[t];
+        }
+        if (t == t1) {
+            br = re[t];
+            bi = im[t];
+        }
+    }
+    ar = __shfl_sync(kFull, ar, j0 / K);
+    ai = __shfl_sync(kFull, ai, j0 / K);
+    br = __shfl_sync(kFull, br, (j0 + 1) / K);
+    bi = __shfl_sync(kFull, bi, (j0 + 1) / K);
+    if (lane == 0) {
+        const double w0 = (1.0 - obs.ft[k]) * w_row[j0];
+        const double w1 = obs.ft[k] * w_row[j0 + 1];
+        const double cr = w0 * (double)ar + w1 * (double)br;
+        const double ci = w0 * (double)ai + w1 * (double)bi;
+        const double wr = slot ? obs.wr1[k] : obs.wr0[k];
+        const long long sample = *(volatile const long long *)sample_ctr + sample_offset;
+        double *dst = wave + ((size_t)k * cap + sample) * 4 + 2 * slot;
+        dst[0] = wr * cr;
+        dst[1] = wr * ci;
+    }
+}
+
+// Every observer slot at column i.
 template <typename T, int K>
 __device__ __forceinline__ void observe(int i, int lane, const T (&o)[4][K], const ObsDev &obs,
                                         double *wave, int64_t cap, const long long *sample_ctr,
@@ -298,33 +342,7 @@ __device__ __forceinline__ void observe(int i, int lane, const T (&o)[4][K], con
     for (int k = 0; k < obs.n; ++k) {
         const int slot = (i == obs.i0[k]) ? 0 : ((i == obs.i0[k] + 1) ? 1 : -1);
         if (slot < 0) continue;
-        const int j0 = obs.j0[k];
-        const double w0 = (1.0 - obs.ft[k]) * w_row[j0];
-        const double w1 = obs.ft[k] * w_row[j0 + 1];
-        double cr = 0.0, ci = 0.0;
-#pragma unroll
-        for (int t = 0; t < K; ++t) {
-            const int r = lane * K + t;
-            if (r == j0) {
-                cr += w0 * (double)o[0][t];
-                ci += w0 * (double)o[1][t];
-            } else if (r == j0 + 1) {
-                cr += w1 * (double)o[0][t];
-                ci += w1 * (double)o[1][t];
-            }
-        }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            cr += __shfl_xor_sync(kFull, cr, off);
-            ci += __shfl_xor_sync(kFull, ci, off);
-        }
-        if (lane == 0) {
-            const double wr = slot ? obs.wr1[k] : obs.wr0[k];
-            const long long sample = *(volatile const long long *)sample_ctr + sample_offset;
-            double *dst = wave + ((size_t)k * cap + sample) * 4 + 2 * slot;
-            dst[0] = wr * cr;
-            dst[1] = wr * ci;
-        }
+        observe_one<T, K>(lane, k, slot, o[0], o[1], obs, wave, cap, sample_ctr, w_row, sample_offset);
     }
 }
 

@@ -577,22 +577,33 @@ constexpr size_t multi_smem_bytes()
     return (size_t)W * (LV + 1) * kSlotCols * 32 * K * sizeof(T);
 }
 
-template <typename T, int K, int W, int LV>
-__device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, const T *__restrict__ u_in,
-                                            T *__restrict__ u_out, const T *__restrict__ half,
-                                            const T *__restrict__ node, int Nr, T en,
-                                            const WaveArgs &wa, int mask, const int (&off)[LV])
+// The four-step sweep copies the Phi values of up to kObsCols observer
+// columns per warp (held in registers; -1: none) to a scratch area at the
+// levels where an outer step ends, and forms the waveform samples from there
+// after its loop.  Sampling inside the loop, at every column checked for an
+// observer, cost a fifth of the sweep's time, and the warps holding an
+// observer set the pace of the persistent launch.  A call whose observers put
+// more than kObsCols columns in one warp's range runs in pairs of steps
+// instead (multi_obs_fit).
+constexpr int kObsCols = 4;
+
+// Scratch per block: per warp, column slot and level, Phi_R and Phi_I (2 NP).
+template <int K, int LV>
+constexpr size_t multi_obs_scratch_elems_per_warp()
+{
+    return (size_t)kObsCols * LV * 2 * 32 * K;
+}
+
+template <typename T, int K, int LV>
+__device__ __forceinline__ void multi_body(T *ring, int i0, int i1, int lane, const T *__restrict__ u_in,
+                                           T *__restrict__ u_out, const T *__restrict__ half,
+                                           const T *__restrict__ node, int Nr, T en, int mask,
+                                           const int (&oc)[kObsCols], T *__restrict__ scr)
 {
     constexpr int NP = 32 * K;
     constexpr int S = LV + 1;
     constexpr size_t SP = 4 * NP;
-    const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    T *ring = reinterpret_cast<T *>(sh_raw) + (size_t)wib * S * kSlotCols * NP;
-    int i0, i1, left;
-    warp_range<W>(Nr, wib, &i0, &i1, &left);
     const int row = lane * K;
-    if (i1 <= i0) return;
     T hm[LV][4][K];   // level l + 1: the half node formed at the last position
     T um[LV][4][K];   // level l: the value formed at the last position
 #pragma unroll
@@ -622,6 +633,10 @@ __device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, const T *__re
             load_state<T, K, true>(u_in + (size_t)(p + 1) * SP + row, cn);
         else
             zero_col<T, K>(cn);
+        // the levels without branches: every node and half node is formed
+        // (a ring slot is in range for any column) and the values outside a
+        // level's columns are then replaced by zero; the stores follow
+        T lv[LV][2][K];   // Phi at each level, for the waveform copies
 #pragma unroll
         for (int l = 1; l <= LV; ++l) {
             const int c = p - l;
@@ -629,29 +644,95 @@ __device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, const T *__re
             if (sl < 0) sl += S;
             const T *tab = ring + sl * kSlotCols * NP;   // tables of column c
             T hp[4][K], uc[4][K];
-            if (c >= i0 - (LV - l) - 1 && c >= 0 && c + 1 < Nr)
-                half_node<T, K>(um[l - 1], cu, tab + row, hp);
-            else
-                zero_col<T, K>(hp);
-            if (c >= i0 - (LV - l) && c >= 1 && c <= Nr - 2)
-                full_node<T, K>(hm[l - 1], hp, um[l - 1], tab + kSlotNode * NP + row, en, uc);
-            else
-                zero_col<T, K>(uc);
-            if (l == LV && c >= i0) store_col<T, K>(u_out + (size_t)c * SP + row, uc);
-            if (((mask >> (l - 1)) & 1) && c >= i0 && c < i1)
-                observe<T, K>(c, lane, uc, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, off[l - 1]);
+            half_node<T, K>(um[l - 1], cu, tab + row, hp);
+            full_node<T, K>(hm[l - 1], hp, um[l - 1], tab + kSlotNode * NP + row, en, uc);
+            const bool hv = c >= i0 - (LV - l) - 1 && c >= 0 && c + 1 < Nr;
+            const bool nv = c >= i0 - (LV - l) && c >= 1 && c <= Nr - 2;   // implies hv
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int t = 0; t < K; ++t) {
                     um[l - 1][q][t] = cu[q][t];
-                    hm[l - 1][q][t] = hp[q][t];
-                    cu[q][t] = uc[q][t];
+                    hm[l - 1][q][t] = hv ? hp[q][t] : T(0);
+                    cu[q][t] = nv ? uc[q][t] : T(0);
                 }
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+                lv[l - 1][0][t] = cu[0][t];
+                lv[l - 1][1][t] = cu[1][t];
+            }
         }
+        if (p - LV >= i0) store_col<T, K>(u_out + (size_t)(p - LV) * SP + row, cu);
+        if (mask)
+#pragma unroll
+            for (int l = 1; l <= LV; ++l)
+                if ((mask >> (l - 1)) & 1)
+#pragma unroll
+                    for (int h = 0; h < kObsCols; ++h)
+                        if (p - l == oc[h]) {
+                            T *d = scr + ((size_t)h * LV + (l - 1)) * 2 * NP + row;
+                            stk<T, K>(d, lv[l - 1][0]);
+                            stk<T, K>(d + NP, lv[l - 1][1]);
+                        }
         cur = nxt;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// The sweep, with the waveform samples formed after its loop (see kObsCols).
+template <typename T, int K, int W, int LV>
+__device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, const T *__restrict__ u_in,
+                                            T *__restrict__ u_out, const T *__restrict__ half,
+                                            const T *__restrict__ node, int Nr, T en,
+                                            const WaveArgs &wa, int mask, const int (&off)[LV],
+                                            T *__restrict__ scr)
+{
+    constexpr int NP = 32 * K;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    T *ring = reinterpret_cast<T *>(sh_raw) + (size_t)wib * (LV + 1) * kSlotCols * NP;
+    int i0, i1, left;
+    warp_range<W>(Nr, wib, &i0, &i1, &left);
+    if (i1 <= i0) return;
+    // this warp's distinct observer columns (the host made sure there are at
+    // most kObsCols)
+    int oc[kObsCols];
+#pragma unroll
+    for (int h = 0; h < kObsCols; ++h) oc[h] = -1;
+    int n = 0;
+    if (mask && wa.write)
+        for (int k = 0; k < wa.obs.n; ++k)
+            for (int sl = 0; sl < 2; ++sl) {
+                const int col = wa.obs.i0[k] + sl;
+                if (col < i0 || col >= i1) continue;
+                bool seen = false;
+#pragma unroll
+                for (int h = 0; h < kObsCols; ++h) seen |= (oc[h] == col);
+                if (!seen && n < kObsCols) {
+#pragma unroll
+                    for (int h = 0; h < kObsCols; ++h)
+                        if (h == n) oc[h] = col;
+                    ++n;
+                }
+            }
+    constexpr size_t kWarpScr = (size_t)kObsCols * LV * 2 * NP;   // per warp
+    T *wscr = scr + (size_t)(blockIdx.x * W + wib) * kWarpScr;
+    multi_body<T, K, LV>(ring, i0, i1, lane, u_in, u_out, half, node, Nr, en, mask, oc, wscr);
+    if (n == 0) return;
+    const int row = lane * K;
+#pragma unroll
+    for (int h = 0; h < kObsCols; ++h) {
+        if (oc[h] < 0) continue;
+#pragma unroll
+        for (int l = 0; l < LV; ++l)
+            if ((mask >> l) & 1) {
+                const T *d = wscr + ((size_t)h * LV + l) * 2 * NP + row;
+                T v[4][K];
+                ldk<T, K>(d, v[0]);
+                ldk<T, K>(d + NP, v[1]);
+                observe<T, K>(oc[h], lane, v, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, off[l]);
+            }
+    }
 }
 
 // Groups of LV steps in one cooperative launch, the blocks waiting for their
@@ -663,7 +744,7 @@ template <typename T, int K, int W, int LV>
 __global__ void __launch_bounds__(W * 32, 1)
 lw_multi_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__restrict__ node,
                            int Nr, T en, const WaveArgs wa, int n_groups, int k, unsigned int *flags,
-                           int *err)
+                           int *err, T *scr)
 {
     extern __shared__ __align__(16) unsigned char sh_raw[];
     for (int g = 0; g < n_groups; ++g) {
@@ -677,7 +758,7 @@ lw_multi_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__
             if (wa.write && (t + l + 1) % k == 0) mask |= 1 << l;
             off[l] = (t + l + 1) / k - 1;
         }
-        multi_sweep<T, K, W, LV>(sh_raw, in, out, half, node, Nr, en, wa, mask, off);
+        multi_sweep<T, K, W, LV>(sh_raw, in, out, half, node, Nr, en, wa, mask, off, scr);
         if (g + 1 < n_groups && !neighbour_barrier(flags, (unsigned)(g + 1), err)) break;
     }
     if (wa.write) advance_sample(wa, (LV * n_groups) / k);
@@ -952,7 +1033,7 @@ namespace {
 
 template <typename T, int K, int W>
 cudaError_t launch_multi_persistent_w(const StepLaunch &L, void *u_other, int n_groups, int k,
-                                      unsigned int *flags, int *err, cudaStream_t st)
+                                      unsigned int *flags, int *err, void *scratch, cudaStream_t st)
 {
     constexpr size_t smem = multi_smem_bytes<T, K, W, kSweepLevels>();
     static cudaError_t e0 = cudaFuncSetAttribute(lw_multi_persistent_kernel<T, K, W, kSweepLevels>,
@@ -970,7 +1051,8 @@ cudaError_t launch_multi_persistent_w(const StepLaunch &L, void *u_other, int n_
     const T *half = (const T *)L.half, *node = (const T *)L.node;
     int Nr = L.Nr;
     T en = (T)(0.5 * L.dt_inner);
-    void *args[] = {&u0, &u1, &half, &node, &Nr, &en, &wa, &n_groups, &k, &flags, &err};
+    T *scr = (T *)scratch;
+    void *args[] = {&u0, &u1, &half, &node, &Nr, &en, &wa, &n_groups, &k, &flags, &err, &scr};
     return cudaLaunchCooperativeKernel((const void *)lw_multi_persistent_kernel<T, K, W, kSweepLevels>,
                                        dim3(L.blocks), dim3(W * 32), args, smem, st);
 }
@@ -987,16 +1069,54 @@ int multi_grid_shape(int precision, int K, int Nr, int num_sms, int *warps)
 
 int multi_levels() { return kSweepLevels; }
 
+size_t multi_obs_scratch_bytes(int K, int blocks, int warps)
+{
+    return multi_obs_scratch_elems_per_warp<kMaxK, kSweepLevels>() / kMaxK * K * sizeof(float) *
+           (size_t)blocks * warps;
+}
+
+// Whether no warp of the four-step sweep's grid (blocks x warps, the column
+// split of warp_range) holds more than kObsCols distinct observer columns.
+bool multi_obs_fit(int Nr, int blocks, int warps, const int *obs_i0, int nobs)
+{
+    const int G = warps / 4;
+    for (int b = 0; b < blocks; ++b) {
+        const int b0 = (int)(((long long)b * Nr) / blocks), b1 = (int)(((long long)(b + 1) * Nr) / blocks);
+        const int C = b1 - b0;
+        int start = b0;
+        for (int w = 0; w < warps; ++w) {
+            const int p = w % 4, q = w / 4;
+            const int cp = ((p + 1) * C) / 4 - (p * C) / 4;
+            const int c = ((q + 1) * cp) / G - (q * cp) / G;
+            int cols[2 * kMaxObservers], n = 0;
+            for (int k = 0; k < nobs; ++k)
+                for (int sl = 0; sl < 2; ++sl) {
+                    const int col = obs_i0[k] + sl;
+                    if (col < start || col >= start + c) continue;
+                    bool seen = false;
+                    for (int h = 0; h < n; ++h) seen |= cols[h] == col;
+                    if (!seen) cols[n++] = col;
+                }
+            if (n > kObsCols) return false;
+            start += c;
+        }
+    }
+    return true;
+}
+
 cudaError_t launch_multi_persistent(const StepLaunch &L, void *u_other, int n_groups, int k,
-                                    unsigned int *flags, int *err, cudaStream_t st)
+                                    unsigned int *flags, int *err, void *scratch, cudaStream_t st)
 {
     if (L.precision != 1) return cudaErrorInvalidValue;
     if (L.K == 1 && L.warps == multi_warps<float, 1>())
-        return launch_multi_persistent_w<float, 1, multi_warps<float, 1>()>(L, u_other, n_groups, k, flags, err, st);
+        return launch_multi_persistent_w<float, 1, multi_warps<float, 1>()>(L, u_other, n_groups, k, flags, err,
+                                                                            scratch, st);
     if (L.K == 2 && L.warps == multi_warps<float, 2>())
-        return launch_multi_persistent_w<float, 2, multi_warps<float, 2>()>(L, u_other, n_groups, k, flags, err, st);
+        return launch_multi_persistent_w<float, 2, multi_warps<float, 2>()>(L, u_other, n_groups, k, flags, err,
+                                                                            scratch, st);
     if (L.K == 4 && L.warps == multi_warps<float, 4>())
-        return launch_multi_persistent_w<float, 4, multi_warps<float, 4>()>(L, u_other, n_groups, k, flags, err, st);
+        return launch_multi_persistent_w<float, 4, multi_warps<float, 4>()>(L, u_other, n_groups, k, flags, err,
+                                                                            scratch, st);
     return cudaErrorInvalidValue;
 }
 

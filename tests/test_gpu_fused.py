@@ -119,6 +119,12 @@ PERSISTENT_CASES = [
     (1, _grid(9800, 32, substeps=1), (9, 2)),               # K = 1: 2 sweeps + a single step
     (1, _grid(2500, 128, substeps=4), (3, 1)),              # K = 4: 3 sweeps; 1 sweep
     (1, _grid(5000, 64, substeps=8), (2, 3)),               # k = 8: 4 sweeps; 6 sweeps
+    # observers at one r* and several theta share their two columns (the sweep's samples)
+    (1, _grid(4901, 64, substeps=2, observers=((100.0, 0.7), (100.0, 1.6), (100.0, 2.5))), (6,)),
+    # four r* two columns apart put seven observer columns in one warp's range:
+    # those calls run in pairs of steps
+    (1, _grid(9801, 64, substeps=2, observers=((100.0, 0.7), (100.125, 1.6), (100.25, 2.5),
+                                               (100.375, 1.1))), (6, 3)),
 ]
 
 
