@@ -69,8 +69,8 @@ MEASURED_TRAFFIC = {
     # one launch of the one-step kernel: 333.910272 + 37.338880 MB
     ("kerr_a0.9_25601x64_38400steps", 0): (333.910272e6 + 37.338880e6,
                                            "profiles/lw_step_f64_kerr_25601x64.md"),
-    # one launch of 50 sweeps of four steps: 8.633103 + 1.269226 GB
-    ("kerr_a0.9_25601x64_38400steps", 1): ((8.633103104e9 + 1.269225728e9) / 50,
+    # one launch of 50 sweeps of four steps: 8.628704 + 1.277802 GB
+    ("kerr_a0.9_25601x64_38400steps", 1): ((8.628704000e9 + 1.277802240e9) / 50,
                                            "profiles/lw_multi_persistent_f32_kerr_25601x64.md"),
 }
 # FP32 on the Kerr workload: every inner step of the solve in one cooperative

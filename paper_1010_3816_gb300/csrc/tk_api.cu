@@ -94,6 +94,16 @@ tk_status enter(tk_solver *S)
     return TK_OK;
 }
 
+// w(theta) of the evolved variable (Phi = w Phi^; 1 for the literal one), as
+// the coefficient precompute writes it to the device for each row.
+static double row_weight(const tk_solver *S, double th)
+{
+    if (S->variable == 0) return 1.0;
+    const int s = S->kerr.s, m = S->kerr.m;
+    const double sh = sin(0.5 * th), ch = cos(0.5 * th);
+    return pow(2.0 * sh * sh, 0.5 * fabs((double)(m + s))) * pow(2.0 * ch * ch, 0.5 * fabs((double)(m - s)));
+}
+
 void fill_launch(const tk_solver *S, tk::StepLaunch &L)
 {
     L.precision = S->precision;
@@ -113,12 +123,20 @@ void fill_launch(const tk_solver *S, tk::StepLaunch &L)
     L.sample_ctr = S->ctr;
     L.done_ctr = (unsigned int *)(S->ctr + 1);
     L.obs.n = S->nobs;
+    const double dth = M_PI / S->Nth;
     for (int k = 0; k < S->nobs; ++k) {
         L.obs.i0[k] = S->obs[k].i0;
         L.obs.j0[k] = S->obs[k].j0;
         L.obs.wr0[k] = 1.0 - S->obs[k].fr;
         L.obs.wr1[k] = S->obs[k].fr;
         L.obs.ft[k] = S->obs[k].ft;
+        const int j0 = S->obs[k].j0;
+        const double wa = row_weight(S, (j0 + 0.5) * dth), wb = row_weight(S, (j0 + 1.5) * dth);
+        for (int sl = 0; sl < 2; ++sl) {
+            const double wr = sl ? L.obs.wr1[k] : L.obs.wr0[k];
+            L.obs.c0[k][sl] = (float)(wr * (1.0 - S->obs[k].ft) * wa);
+            L.obs.c1[k][sl] = (float)(wr * S->obs[k].ft * wb);
+        }
     }
 }
 

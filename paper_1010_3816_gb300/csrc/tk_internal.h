@@ -57,6 +57,9 @@ struct ObsDev {
     double wr0[kMaxObservers];      // 1 - fr
     double wr1[kMaxObservers];      // fr
     double ft[kMaxObservers];       // theta weight fth
+    // FP32 sweeps: the sample's weights of rows j0 and j0 + 1 for slot 0 and 1,
+    // wr_slot * (1 - fth) * w(theta_j0) and wr_slot * fth * w(theta_j0+1)
+    float c0[kMaxObservers][2], c1[kMaxObservers][2];
 };
 
 // ---- coefficient precompute (tk_coeffs.cu) ----

@@ -299,8 +299,8 @@ __device__ __forceinline__ void observe_one(int lane, int k, int slot, const T (
                                             int sample_offset)
 {
     // only rows j0 and j0 + 1 contribute: fetch them from the lanes that hold
-    // them (two shuffles) and let lane 0 do the few FP64 operations, instead
-    // of a reduction over the warp, whose FP64 adds hold GB300's FP64 pipe for
+    // them (two shuffles) and let lane 0 do the few operations, instead of a
+    // reduction over the warp, whose FP64 adds hold GB300's FP64 pipe for
     // microseconds
     const int j0 = obs.j0[k];
     const int t0 = j0 % K, t1 = (j0 + 1) % K;
@@ -321,15 +321,22 @@ __device__ __forceinline__ void observe_one(int lane, int k, int slot, const T (
     br = __shfl_sync(kFull, br, (j0 + 1) / K);
     bi = __shfl_sync(kFull, bi, (j0 + 1) / K);
     if (lane == 0) {
-        const double w0 = (1.0 - obs.ft[k]) * w_row[j0];
-        const double w1 = obs.ft[k] * w_row[j0 + 1];
-        const double cr = w0 * (double)ar + w1 * (double)br;
-        const double ci = w0 * (double)ai + w1 * (double)bi;
-        const double wr = slot ? obs.wr1[k] : obs.wr0[k];
         const long long sample = *(volatile const long long *)sample_ctr + sample_offset;
         double *dst = wave + ((size_t)k * cap + sample) * 4 + 2 * slot;
-        dst[0] = wr * cr;
-        dst[1] = wr * ci;
+        if constexpr (sizeof(T) == 4) {
+            // FP32: the weights precomputed on the host, FP32 arithmetic
+            const float c0 = obs.c0[k][slot], c1 = obs.c1[k][slot];
+            dst[0] = (double)fmaf(c1, br, c0 * ar);
+            dst[1] = (double)fmaf(c1, bi, c0 * ai);
+        } else {
+            const double w0 = (1.0 - obs.ft[k]) * w_row[j0];
+            const double w1 = obs.ft[k] * w_row[j0 + 1];
+            const double cr = w0 * (double)ar + w1 * (double)br;
+            const double ci = w0 * (double)ai + w1 * (double)bi;
+            const double wr = slot ? obs.wr1[k] : obs.wr0[k];
+            dst[0] = wr * cr;
+            dst[1] = wr * ci;
+        }
     }
 }
 

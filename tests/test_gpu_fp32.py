@@ -1,8 +1,9 @@
 """FP32 step (TK_PREC_F32): FP32 planes, tables and stencil arithmetic, with
 the coefficient precompute (including the r(r*) inversion) in FP64 and the
-waveform samples accumulated in FP64.  Its error against the FP64 oracle is
-measured and bounded per waveform; the bounds below are the measured errors
-with a safety factor, not parity claims.
+waveform samples formed in FP32 from weights precomputed in FP64 on the host
+(stored as FP64).  Its error against the FP64 oracle is measured and bounded
+per waveform; the bounds below are the measured errors with a safety factor,
+not parity claims.
 """
 import math
 
