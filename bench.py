@@ -80,6 +80,18 @@ FP32_STEPS_PER_SWEEP = 4
 L2_FLUSH_BYTES = 256 << 20          # twice the 129 MB L2
 
 
+def _hbm_peak():
+    """Measured HBM copy bandwidth of the GB300s (GB/s) and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "6.8 TB/s (of fallback: no MEASURED_PEAKS.json)"
+
+
+HBM_GBS, HBM_SRC = _hbm_peak()
+
+
 class L2Flush:
     """Writes a buffer twice the size of L2 on the stream, evicting every line
     the previous step left behind."""
@@ -233,17 +245,18 @@ def _variant_name(w, base) -> str:
     return "_".join(parts)
 
 
-def _config(w, args, world):
+def _config(w, args, world, precision=None):
+    precision = args.precision if precision is None else precision
     return {"workload": w.name, "a": w.a, "M": w.M, "s": w.s, "m": w.m, "Nr": w.Nr,
             "Ntheta": w.Ntheta, "rstar": [w.rs_min, w.rs_max], "dt": w.dt,
             "outer_steps": args.outer_steps or w.steps, "substeps": w.substeps,
             "variable": "regularised" if w.variable else "literal",
-            "precision": "f32" if args.precision else "f64",
+            "precision": "f32" if precision else "f64",
             "observers": [list(o) for o in w.observers],
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
             "l2": L2_NOTE + "; working set: state 2x{:.1f} MB + tables {:.1f} MB".format(
-                w.points * STATE_BYTES_PER_UPDATE[args.precision] / 1e6,
-                w.points * TABLE_BYTES_PER_UPDATE[args.precision] / 1e6)}
+                w.points * STATE_BYTES_PER_UPDATE[precision] / 1e6,
+                w.points * TABLE_BYTES_PER_UPDATE[precision] / 1e6)}
 
 
 def _clock_checked(clk):
@@ -252,11 +265,14 @@ def _clock_checked(clk):
     return bad
 
 
-def run_batched(args, tk, torch, rank, world, local):
+def run_batched(args, tk, torch, rank, world, local, steps=None, warmup=None, emit=True):
     """The 24-instance batch: instances sharded across ranks by cost, each
     rank's share advanced by one tk_batch (one launch per inner tick, graph
     replay, autotuned segment length); compared with running the same
-    instances one after another through tk_step."""
+    instances one after another through tk_step.  Prints the JSON line (emit)
+    or returns its fields."""
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
     from paper_1010_3816_gb300 import distributed as D
     inst_all = batched_instances()
     if args.instances:
@@ -304,7 +320,7 @@ def run_batched(args, tk, torch, rank, world, local):
                 tk.tk_extract(g.h, k, a, b)
 
     flush = L2Flush(torch)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush()
         solve(False)
     torch.cuda.synchronize()
@@ -314,7 +330,7 @@ def run_batched(args, tk, torch, rank, world, local):
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush()
         solve(True)
     t1.record(stream)
@@ -323,7 +339,7 @@ def run_batched(args, tk, torch, rank, world, local):
     clk = clocks.stop()
     ms = D.reduce_max(t0.elapsed_time(t1), device="cuda")
     total_updates = D.reduce_sum(updates, device="cuda")
-    value = total_updates * args.steps / (ms * 1e-3)
+    value = total_updates * steps / (ms * 1e-3)
     kern_s = statistics.mean(a.elapsed_time(b) for a, b in ev) * 1e-3
     # the same instances through tk_step, one after another
     solve(False, batched=False)
@@ -338,10 +354,11 @@ def run_batched(args, tk, torch, rank, world, local):
     f_clk = (clk.get("sm_mhz") or 2070.0) * 1e6
     achieved = FP64_FLOP_PER_UPDATE * updates / kern_s / 1e12
     peak = NUM_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * f_clk / 1e12
+    line = None
     if rank == 0:
         line = {
             "metric": "grid-point updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": f"batched_{len(inst_all)}_instances", "instances": len(inst_all),
@@ -356,14 +373,16 @@ def run_batched(args, tk, torch, rank, world, local):
                          "frac": achieved / peak, "traffic": None, "kernel": "batch_step_kernel<double>",
                          "peak_source": "152 SMs x 2 DFMA/clk (measured) x 2 flop x median SM clock"},
             "plain_tk_step": {"value": plain, "unit": "updates/s",
-                              "batched_over_plain": (updates / kern_s) / plain},
+                              "what": "the same instances through tk_step one after another"},
+            "ratio_vs_sequential_tk_step": (updates / kern_s) / plain,
             "cpu_baseline": None, "e2e": None, "clocks": clk,
-            "gpu_launches": args.steps * (n_outer * info["kmax"] + 3 * len(inst) +
+            "gpu_launches": steps * (n_outer * info["kmax"] + 3 * len(inst) +
                                           sum(len(o) for o in outs)),
         }
-        print(json.dumps(line))
+        if emit:
+            print(json.dumps(line))
     batch.close()
-    return 0
+    return 0 if emit else line
 
 
 def run_adjoint(args, tk, torch, rank, world, local):
@@ -516,6 +535,8 @@ def main() -> int:
                     help="batched workload: the first N of its 24 instances (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra-arms", action="store_true",
+                    help="Kerr FP64 run: skip the FP32 and batched arms that follow it")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     if w is not None:
@@ -549,10 +570,80 @@ def main() -> int:
         if dist:
             dist.destroy_process_group()
         return rc
+    main_arm = measure_solve(args, tk, torch, w, args.precision, args.steps, args.warmup, rank,
+                             world, local, dist, not args.no_e2e)
+    line = None
+    if rank == 0:
+        cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(main_arm["w"],
+                                                                           args.cpu_sample_steps)
+        line = {
+            "metric": "grid-point updates/s", "value": main_arm["value"], "unit": "updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": main_arm["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if args.precision else "f64", "data": "synthetic",
+            "config": _config(main_arm["w"], args, world, args.precision),
+            "roofline": main_arm["roofline"], "roofline_hbm": main_arm["roofline_hbm"],
+            "parity_vs_oracle_full_run": main_arm["parity"],
+            "cpu_baseline": cpu, "e2e": main_arm["e2e"], "clocks": main_arm["clocks"],
+            "gpu_launches": main_arm["gpu_launches"],
+        }
+    # the metric's other two forms on the same GPU, after the FP64 arm: FP32 at
+    # its stated waveform error, and the batched instances against the same
+    # instances through tk_step one after another
+    extra = (args.workload == "kerr" and args.precision == 0 and not args.no_extra_arms and
+             w == WORKLOADS["kerr"] and not args.outer_steps)
+    if extra:
+        f32 = measure_solve(args, tk, torch, w, 1, args.steps, args.warmup, rank, world, local, dist,
+                            not args.no_e2e)
+        if rank == 0:
+            line["fp32"] = {
+                "value": f32["value"], "unit": "updates/s", "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": f32["ms_per_step"],
+                "ratio_vs_fp64": f32["value"] / main_arm["value"],
+                "e2e": f32["e2e"],
+                "e2e_ratio_vs_fp64": (f32["e2e"]["value"] / main_arm["e2e"]["value"]
+                                      if f32["e2e"] and main_arm["e2e"] else None),
+                "error_vs_fp64_oracle_full_run": f32["parity"],
+                "roofline": f32["roofline"], "roofline_hbm": f32["roofline_hbm"],
+                "clocks": f32["clocks"], "gpu_launches": f32["gpu_launches"],
+                "config": _config(w, args, world, 1)}
+        bsteps = min(args.steps, 5)
+        bat = run_batched(args, tk, torch, rank, world, local, steps=bsteps, warmup=3, emit=False)
+        if rank == 0:
+            line["batched"] = bat
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+# Stored full-length oracle run of the Kerr workload (tests/golden/make_kerr_golden.py).
+GOLDEN_KERR = os.path.join(ROOT, "tests", "golden", "kerr_25601x64_oracle.npz")
+
+
+def _parity_full_run(w, waves):
+    """Relative L2 of the waveforms against the oracle's stored full run of the
+    Kerr workload, or None when this solve is not that run."""
+    if w != WORKLOADS["kerr"] or not os.path.exists(GOLDEN_KERR):
+        return None
+    ref = np.load(GOLDEN_KERR)
+    out = {"reference": "tests/golden/kerr_25601x64_oracle.npz (FP64 CPU oracle, all 38400 outer "
+                        "steps)"}
+    for k, key in enumerate(("wave0", "wave1")):
+        out[key + "_rel_l2"] = float(np.linalg.norm(waves[k] - ref[key]) / np.linalg.norm(ref[key]))
+    out["observers"] = [list(o) for o in w.observers]
+    return out
+
+
+def measure_solve(args, tk, torch, w, precision, steps, warmup, rank, world, local, dist, do_e2e):
+    """Whole solves of workload w at the given precision: `warmup` untimed,
+    then `steps` timed (device-resident inputs, L2 flushed before each), then
+    the same through host buffers (e2e).  Returns the numbers of one arm."""
     n_outer = args.outer_steps or w.steps
     stream = torch.cuda.current_stream()
     solver = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
-                       substeps=w.substeps, variable=w.variable, precision=args.precision,
+                       substeps=w.substeps, variable=w.variable, precision=precision,
                        stream=stream.cuda_stream)
     if w.substeps == 0:
         # substeps chosen by the solver's stability bound at the precompute
@@ -563,9 +654,9 @@ def main() -> int:
     # four in one persistent launch (whole outer steps), the rest as pairs in
     # a second one and an odd last step alone; FP64 launches one step at a
     # time on this grid
-    spl = FP32_STEPS_PER_SWEEP if args.precision == 1 else 1
+    spl = FP32_STEPS_PER_SWEEP if precision == 1 else 1
     inner_steps = n_outer * w.substeps
-    if args.precision == 1:
+    if precision == 1:
         unit = w.substeps // math.gcd(spl, w.substeps)
         sweeps = inner_steps // spl // unit * unit
         rest = inner_steps - sweeps * spl
@@ -598,7 +689,7 @@ def main() -> int:
             tk.tk_extract(solver.h, k, a, b)
 
     flush = L2Flush(torch)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush()
         solve_device(False)
     torch.cuda.synchronize()
@@ -610,7 +701,7 @@ def main() -> int:
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush()
         solve_device(True)
     t_end.record(stream)
@@ -624,19 +715,24 @@ def main() -> int:
         t = torch.tensor([ms], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * updates * args.steps / (ms * 1e-3)
+    value = world * updates * steps / (ms * 1e-3)
     step_ms = [a.elapsed_time(b) for a, b in ev_step]
     kern_s = statistics.mean(step_ms) * 1e-3 / (n_outer * w.substeps)   # per inner step
     pts = w.points
     f_clk = (clk.get("sm_mhz") or 2070.0) * 1e6
-    traffic, traffic_src = MEASURED_TRAFFIC.get((w.name, args.precision), (None, None))
-    if args.precision == 0:
+    traffic, traffic_src = MEASURED_TRAFFIC.get((w.name, precision), (None, None))
+    if precision == 0:
         achieved = FP64_FLOP_PER_UPDATE * pts / kern_s / 1e12
         peak = NUM_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * f_clk / 1e12
+        probe = fp64_probe(tk, f_clk)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "lw_step_kernel<double>",
-                "peak_source": "152 SMs x 2 DFMA/clk (measured) x 2 flop x median SM clock "
-                               f"{f_clk / 1e6:.0f} MHz",
+                "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x median SM clock "
+                               f"{f_clk / 1e6:.0f} MHz (GB300 FP64 FMA issue rate; "
+                               "profiles/fp64_pipe_peak.md)",
+                "peak_measured": probe["tflops"],
+                "frac_of_measured": achieved / probe["tflops"],
+                "peak_measured_source": "tk_probe_fp64_fma in this run: " + probe["how"],
                 "traffic_source": traffic_src, "flop_per_update": FP64_FLOP_PER_UPDATE,
                 "fp64_issue_frac": FP64_INSTR_PER_UPDATE * pts / kern_s /
                 (NUM_SMS * FP64_FMA_PER_CLK_PER_SM * f_clk),
@@ -649,22 +745,22 @@ def main() -> int:
         sweep_s = spl * kern_s
         alg = (STATE_BYTES_PER_UPDATE[1] + TABLE_BYTES_PER_UPDATE[1]) * pts
         achieved = alg / sweep_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": 6794.1, "unit": "GB/s",
-                "frac": achieved / 6794.1, "traffic": traffic,
+        roof = {"bound": "hbm", "achieved": achieved, "peak": HBM_GBS, "unit": "GB/s",
+                "frac": achieved / HBM_GBS, "traffic": traffic,
                 "kernel": "lw_multi_persistent_kernel<float>",
                 "algorithmic_bytes_per_sweep": alg, "inner_steps_per_sweep": spl,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+                "peak_source": HBM_SRC,
                 "traffic_source": traffic_src, "sweep_us": sweep_s * 1e6}
-    sb = STATE_BYTES_PER_UPDATE[args.precision] * pts / kern_s / 1e9
-    tb = TABLE_BYTES_PER_UPDATE[args.precision] * pts / kern_s / 1e9
-    roof_hbm = {"bound": "hbm", "achieved": sb, "peak": 6794.1, "unit": "GB/s",
-                "frac": sb / 6794.1, "state_bytes_per_update": STATE_BYTES_PER_UPDATE[args.precision],
-                "table_gbs": tb, "table_bytes_per_update": TABLE_BYTES_PER_UPDATE[args.precision],
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+    sb = STATE_BYTES_PER_UPDATE[precision] * pts / kern_s / 1e9
+    tb = TABLE_BYTES_PER_UPDATE[precision] * pts / kern_s / 1e9
+    roof_hbm = {"bound": "hbm", "achieved": sb, "peak": HBM_GBS, "unit": "GB/s",
+                "frac": sb / HBM_GBS, "state_bytes_per_update": STATE_BYTES_PER_UPDATE[precision],
+                "table_gbs": tb, "table_bytes_per_update": TABLE_BYTES_PER_UPDATE[precision],
+                "peak_source": HBM_SRC}
 
     # end to end through the public API: host input planes (pinned), host waveform read-back
     e2e = None
-    if not args.no_e2e:
+    if do_e2e:
         h_re = torch.from_numpy(re).pin_memory()
         h_im = torch.from_numpy(im).pin_memory()
         h_out = [(np.zeros(n_outer), np.zeros(n_outer)) for _ in w.observers]
@@ -683,7 +779,7 @@ def main() -> int:
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush()
             solve_host()
         torch.cuda.synchronize()
@@ -692,28 +788,29 @@ def main() -> int:
             t = torch.tensor([es], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             es = float(t.item())
-        e2e = {"value": world * updates * args.steps / es, "unit": "updates/s",
+        e2e = {"value": world * updates * steps / es, "unit": "updates/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": 1e3 * es / args.steps}
+               "ms_per_step": 1e3 * es / steps}
 
     solver.check_finite()
-    if rank == 0:
-        cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(w, args.cpu_sample_steps)
-        line = {
-            "metric": "grid-point updates/s", "value": value, "unit": "updates/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32" if args.precision else "f64", "data": "synthetic",
-            "config": _config(w, args, world), "roofline": roof, "roofline_hbm": roof_hbm,
-            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-            "gpu_launches": launches_per_solve * args.steps,
-        }
-        print(json.dumps(line))
+    parity = None
+    if rank == 0 and not args.outer_steps:
+        parity = _parity_full_run(w, [solver.waveform(k) for k in obs_ids])
     solver.close()
-    if dist:
-        dist.destroy_process_group()
-    return 0
+    return {"w": w, "value": value, "ms_per_step": ms / steps, "roofline": roof,
+            "roofline_hbm": roof_hbm, "e2e": e2e, "clocks": clk, "parity": parity,
+            "gpu_launches": launches_per_solve * steps}
 
+
+def fp64_probe(tk, f_clk):
+    """The FP64 FMA pipe's rate measured by the library's microbenchmark
+    (one 512-thread block per SM, 8 independent FMA chains per thread)."""
+    iters = 1 << 17
+    s, flop = tk.tk_probe_fp64_fma(1, 512, iters)
+    tf = flop / s / 1e12
+    return {"tflops": tf, "dfma_per_clk_per_sm": flop / 2 / s / (NUM_SMS * f_clk),
+            "how": f"{flop:.3e} flop in {s * 1e3:.1f} ms ({flop / 2 / s / (NUM_SMS * f_clk):.3f} "
+                   f"DFMA/clk/SM at {f_clk / 1e6:.0f} MHz)"}
 
 if __name__ == "__main__":
     sys.exit(main())

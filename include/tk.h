@@ -66,7 +66,8 @@ enum {
 enum {
     TK_PREC_F64 = 0,        /* FP64 planes, tables and arithmetic                */
     TK_PREC_F32 = 1         /* FP32 planes, tables and stencil arithmetic; FP64
-                               coefficient precompute and waveform samples      */
+                               coefficient precompute, and waveform samples
+                               formed in FP64 from the FP32 state values        */
 };
 
 /* Create a solver for an Nr x Ntheta grid (Sec. 3.2).
@@ -119,9 +120,11 @@ tk_status tk_set_initial_data(tk_solver *S, const double *phi_re, const double *
 tk_status tk_set_initial_gaussian(tk_solver *S, double amp, double center, double width,
                                   double noise_amp, uint64_t seed);
 
-/* Register a waveform observer at (rstar_obs, theta_obs); writes its id.  The
- * sample after every outer step is the bilinear interpolant in (r*, theta) of
- * the physical field Phi = w Phi^ (w = 1 for the literal variable).  The point
+/* Register a waveform observer at (rstar_obs, theta_obs); writes its id.  Not
+ * in the paper, which prints no extraction rule: the sample after every outer
+ * step is taken here as the bilinear interpolant in (r*, theta) of the
+ * physical field Phi = w Phi^ (w = 1 for the literal variable), formed in FP64
+ * for both precisions.  The point
  * must lie in [r*_0, r*_{Nr-1}] x [theta_0, theta_{Ntheta-1}] (TK_ERR_ARG
  * otherwise).  At most 16 observers.  Observers are added after
  * tk_set_initial_data and before the first tk_step (TK_ERR_STATE otherwise);
@@ -134,8 +137,12 @@ tk_status tk_add_observer(tk_solver *S, double rstar_obs, double theta_obs, int 
  * tk_set_steps_per_launch (-1, the default for FP32 and for FP64 grids too
  * small for one block per SM), where every step of the call runs in one
  * cooperative launch and the call synchronizes the stream to check that
- * launch's bounded waits (TK_ERR_INTERNAL if one ran out; the state is then
- * invalid).  Otherwise
+ * launch's bounded waits.  If one ran out, tk_step returns TK_ERR_INTERNAL,
+ * the step and sample counts stay where the call found them (the samples
+ * taken before it stay readable), and the state is invalid: tk_step,
+ * tk_get_state, tk_check_finite, tk_adjoint and tk_param_gradient return
+ * TK_ERR_STATE until tk_set_state or tk_set_initial_data sets it again.
+ * Otherwise
  * whole chunks of outer steps are replayed from a CUDA graph captured on
  * first use (see tk_set_graph_chunk) and the rest are launched one by one.
  * Every path gives identical results.  The first call after tk_add_observer,
@@ -147,28 +154,35 @@ tk_status tk_step(tk_solver *S, int n);
  * c outer steps (rounded up to an even number of launches). */
 tk_status tk_set_graph_chunk(tk_solver *S, int outer_steps);
 
-/* Waveform of observer obs_id: copies the first min(count, capacity) samples
- * into re[], im[] (device pointers if on_device) and writes the total sample
- * count to *count.  re/im may be NULL with capacity 0 to query the count. */
+/* Waveform of observer obs_id (the samples of tk_add_observer; not in the
+ * paper): copies the first min(count, capacity) samples into re[], im[]
+ * (device pointers if on_device) and writes the total sample count to *count.
+ * re/im may be NULL with capacity 0 to query the count.  A host read-out goes
+ * through a device buffer of 16 bytes per sample of the waveform buffer's
+ * capacity, which the solver allocates on the first such call and again only
+ * when that capacity has grown (see tk_extract_noalloc for a read-out that
+ * never allocates); it synchronizes the stream. */
 tk_status tk_extract(tk_solver *S, int obs_id, double *re, double *im, int capacity, int *count,
                      int on_device);
 
-/* Allocation-free read-out of a waveform into host memory (the paper has no
- * counterpart; it is for callers that must not allocate device memory, such
- * as code running while a CUDA graph is being captured, loops whose memory is
- * fixed in advance, or hosts that route all device memory through their own
- * pool -- tk_extract allocates a temporary device buffer on every call).
- * Copies samples [first, first + count) of observer obs_id to re[0..count)
- * and im[0..count) (host pointers, pageable or pinned) and synchronizes the
- * solver's stream.  Device work goes through a 1 MiB array compiled into the
- * library, so count is limited to 65536 per call (TK_ERR_ARG beyond; read a
- * longer waveform in pieces).  The array is shared by every call in the
- * process and keeps the last call's contents: calls whose work overlaps on
- * the GPU (other threads, other streams) race on it and must be serialized
- * by the caller.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Allocates nothing: no cudaMalloc, cudaFree or allocating library
- * call. */
+/* Allocation-free read-out of a waveform into host memory.  The paper has no
+ * counterpart.  It is for callers that must not allocate device memory once
+ * they are set up: hosts that hand all device memory to their own pool and
+ * treat any other allocation as a failure, and loops whose device-memory
+ * budget is fixed in advance (tk_extract allocates its read-out buffer on
+ * first use and when the waveform grows, and a cudaMalloc can also
+ * synchronize the device).  Copies samples [first, first + count) of observer
+ * obs_id to re[0..count) and im[0..count) (host pointers, pageable or pinned),
+ * bit-identical to what tk_extract returns, and synchronizes the solver's
+ * stream.  Device work goes through a 1 MiB array compiled into the library,
+ * so count is limited to 65536 per call (TK_ERR_ARG beyond; read a longer
+ * waveform in pieces).  The array is shared by every call in the process and
+ * keeps the last call's contents: calls whose work overlaps on the GPU (other
+ * threads, other streams) race on it and must be serialized by the caller.
+ * Every call looks up the array's device address (cudaGetSymbolAddress); the
+ * first lookup on a device may load the library's device code, so make the
+ * first call on each device before any stream capture.  Allocates nothing: no
+ * cudaMalloc, cudaFree or allocating library call. */
 tk_status tk_extract_noalloc(tk_solver *S, int obs_id, int first, int count, double *re,
                              double *im);
 
@@ -213,15 +227,20 @@ tk_status tk_adjoint(tk_solver *S, const double *dL_dwave, const double *dL_dfin
 tk_status tk_param_gradient(tk_solver *S, int param, const double *dL_dwave, int on_device,
                             int checkpoint_every, double *grad);
 
-/* Current state as planes4 (4 * Ntheta * Nr doubles), host or device. */
+/* Current state as planes4 (4 * Ntheta * Nr doubles), host or device.  (The
+ * paper's solver keeps its state on the device; this read-back and
+ * tk_set_state are checkpoint and test plumbing, not steps of the method.) */
 tk_status tk_get_state(tk_solver *S, double *planes4, int on_device);
 
 /* Overwrite the state from planes4 (checkpoint restore); keeps observers and
- * the step counter. */
+ * the step counter, and makes an invalid state (see tk_step) valid again. */
 tk_status tk_set_state(tk_solver *S, const double *planes4, int on_device);
 
 /* Largest stable inner step for the current coefficients, and the number of
- * Lax-Wendroff steps per outer step it implies for this solver's dt.  Two
+ * Lax-Wendroff steps per outer step it implies for this solver's dt.  Not in
+ * the paper, which gives no time step; the outer dt is read as the sampling
+ * cadence, split into this many inner steps where the angular source needs
+ * it.  Two
  * limits, both evaluated on the device over every interior node: the radial
  * CFL condition of the Lax-Wendroff scheme, b dt / dr* <= 1, and the angular
  * source term, which the two-step scheme advances like a 2nd-order
@@ -319,6 +338,25 @@ void tk_batch_destroy(tk_batch *B);
  * 2^24 polls.  Runs on the legacy default stream and synchronizes.
  * TK_ERR_ARG for arguments out of range (message in tk_last_error(NULL)). */
 tk_status tk_check_bounded_wait(int n_blocks, int silent, int64_t max_polls, int *timed_out);
+
+/* Measured rate of this GPU's FP64 fused multiply-add pipe (not in the
+ * paper; the roofline of the FP64 step, which is bound by that pipe).  Runs
+ * blocks_per_sm * (SM count) blocks of `threads` threads (a multiple of 32,
+ * <= 1024), each thread advancing 8 independent FP64 FMA chains `iters`
+ * times, on the legacy default stream after a short warm-up launch, and
+ * writes the launch's duration (CUDA events) to *seconds and the FP64 flops
+ * it did (2 per FMA) to *flop.  Allocates and frees a few bytes of device
+ * memory; synchronizes.  TK_ERR_ARG for arguments out of range (message in
+ * tk_last_error(NULL)). */
+tk_status tk_probe_fp64_fma(int blocks_per_sm, int threads, int iters, double *seconds,
+                            double *flop);
+
+/* Test hook, host-side fault injection (not in the paper): the next tk_step
+ * on this solver that runs a persistent launch completes its device work
+ * normally and then reports its bounded waits as having run out, with the
+ * consequences described at tk_step.  For testing a caller's recovery path
+ * without a device fault.  Cleared when it fires. */
+tk_status tk_inject_wait_timeout(tk_solver *S);
 
 /* One-line description of the last error on this solver (never NULL). */
 const char *tk_last_error(const tk_solver *S);

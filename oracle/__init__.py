@@ -5,6 +5,12 @@ CPU-baseline leg of ``bench.py`` may import this package.  It wraps the plain C
 implementation in ``tk_oracle.c`` (FP64, no FMA contraction, no fast-math),
 which shares no code with the CUDA path.
 
+The same unchanged source is also built a second time with FMA contraction
+(``build(fma=True)``, selected per solver by ``Solver(..., build="fma")``): a
+different, equally correct rounding order of the same scheme.  The distance
+between the two builds' runs is the size of the rounding differences any two
+correct implementations of the scheme accumulate over a run.
+
 The state layout is the paper's (Sec. 4): four planes ``qre, qim, pre, pim``,
 each ``[Ntheta][Nr]`` with the r* index fastest.
 """
@@ -21,28 +27,46 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tk_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libtk_oracle.so")
+_SO_FMA = os.path.join(_BUILD, "libtk_oracle_fma.so")
 _lock = threading.Lock()
-_lib_handle = None
+_lib_handles = {}
 
 NCOEF = 9
 COEF_NAMES = ("b", "c1R", "c1I", "c2R", "c2I", "c3R", "c3I", "c4", "c5")
 
 
-def build(force: bool = False) -> str:
+def _fma_flags():
+    """Flags that let gcc contract a*b + c into fused multiply-adds.  aarch64
+    has FMA in its base instruction set; x86-64 needs -mfma to emit one."""
+    import platform
+    flags = ["-ffp-contract=fast"]
+    if platform.machine().lower() in ("x86_64", "amd64"):
+        flags.append("-mfma")
+    return flags
+
+
+def build(force: bool = False, fma: bool = False) -> str:
     """Compile ``tk_oracle.c`` into ``_build/libtk_oracle.so`` (with OpenMP if
-    the compiler supports it).  Returns the path of the shared library."""
+    the compiler supports it).  Returns the path of the shared library.
+
+    With ``fma`` the same source is compiled into ``libtk_oracle_fma.so`` with
+    FMA contraction on (the only change); it serves as a second rounding order
+    of the same arithmetic."""
     os.makedirs(_BUILD, exist_ok=True)
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
-        return _SO
-    base = ["gcc", "-std=gnu11", "-O2", "-ffp-contract=off", "-fno-fast-math",
-            "-fPIC", "-shared", _SRC, "-o", _SO + ".tmp", "-lm"]
+    so = _SO_FMA if fma else _SO
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= os.path.getmtime(_SRC):
+        return so
+    contract = _fma_flags() if fma else ["-ffp-contract=off"]
+    tmp = so + ".%d.tmp" % os.getpid()
+    base = ["gcc", "-std=gnu11", "-O2"] + contract + ["-fno-fast-math",
+            "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
     r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True, text=True)
     if r.returncode != 0:
         r = subprocess.run(base, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("oracle build failed:\n" + r.stderr)
-    os.replace(_SO + ".tmp", _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
 
 
 class Params(C.Structure):
@@ -54,13 +78,19 @@ class Params(C.Structure):
 _dp = C.POINTER(C.c_double)
 
 
-def _lib():
-    global _lib_handle
+def _lib(variant: str = "plain"):
+    """The loaded oracle library: ``"plain"`` (no contraction) or ``"fma"``."""
+    if variant not in ("plain", "fma"):
+        raise ValueError(variant)
     with _lock:
-        if _lib_handle is None:
-            # TKO_SO names an alternative build of tk_oracle.c (used to check
-            # that the pins catch deliberately planted mistakes).
-            lib = C.CDLL(os.environ.get("TKO_SO") or build())
+        if variant not in _lib_handles:
+            if variant == "fma":
+                path = build(fma=True)
+            else:
+                # TKO_SO names an alternative build of tk_oracle.c (used to check
+                # that the pins catch deliberately planted mistakes).
+                path = os.environ.get("TKO_SO") or build()
+            lib = C.CDLL(path)
             lib.tko_tortoise_x.restype = C.c_double
             lib.tko_tortoise_x.argtypes = [C.c_double, C.c_double, C.c_double]
             lib.tko_x_of_rstar.restype = C.c_double
@@ -102,8 +132,8 @@ def _lib():
             lib.tko_set_threads.argtypes = [C.c_int]
             lib.tko_get_threads.restype = C.c_int
             lib.tko_get_threads.argtypes = []
-            _lib_handle = lib
-        return _lib_handle
+            _lib_handles[variant] = lib
+        return _lib_handles[variant]
 
 
 def _ptr(a: np.ndarray):
@@ -190,22 +220,24 @@ class Solver:
     grid is ``rs_min + a*drs`` for ``a < Nr``, the angular grid is
     ``(b + 1/2) pi / Ntheta``; ``dt`` is the outer step, split into
     ``substeps`` Lax-Wendroff steps; ``variable`` 0 evolves the literal
-    field, 1 the pole-regularised one.
+    field, 1 the pole-regularised one.  ``build`` picks the library:
+    ``"plain"`` (no FMA contraction) or ``"fma"`` (the same source contracted).
     """
 
     def __init__(self, *, M=1.0, a=0.0, s=-2, m=2, rs_min, rs_max, Nr, Ntheta, dt,
-                 substeps=1, variable=1):
+                 substeps=1, variable=1, build="plain"):
         self.Nr, self.Ntheta = int(Nr), int(Ntheta)
         drs = (rs_max - rs_min) / (Nr - 1)
         self.params = Params(M, a, s, m, rs_min, drs, Nr, Ntheta, dt, substeps, variable)
-        self._h = _lib().tko_new(C.byref(self.params))
+        self._lib = _lib(build)
+        self._h = self._lib.tko_new(C.byref(self.params))
         if not self._h:
             raise ValueError("oracle rejected the parameters")
 
     def __del__(self):
         h = getattr(self, "_h", None)
         if h:
-            _lib().tko_free(h)
+            self._lib.tko_free(h)
             self._h = None
 
     @property
@@ -217,44 +249,44 @@ class Solver:
         pr = np.ascontiguousarray(phi_re, dtype=np.float64).reshape(shp)
         pi = np.ascontiguousarray(phi_im, dtype=np.float64).reshape(shp)
         if pi_re is None:
-            _lib().tko_set_initial(self._h, _ptr(pr), _ptr(pi), None, None)
+            self._lib.tko_set_initial(self._h, _ptr(pr), _ptr(pi), None, None)
         else:
             qr = np.ascontiguousarray(pi_re, dtype=np.float64).reshape(shp)
             qi = np.ascontiguousarray(pi_im, dtype=np.float64).reshape(shp)
-            _lib().tko_set_initial(self._h, _ptr(pr), _ptr(pi), _ptr(qr), _ptr(qi))
+            self._lib.tko_set_initial(self._h, _ptr(pr), _ptr(pi), _ptr(qr), _ptr(qi))
 
     def add_observer(self, rstar: float, theta: float) -> int:
-        k = _lib().tko_add_observer(self._h, rstar, theta)
+        k = self._lib.tko_add_observer(self._h, rstar, theta)
         if k < 0:
             raise ValueError("observer outside the grid")
         return k
 
     def run(self, n: int) -> None:
-        _lib().tko_run(self._h, int(n))
+        self._lib.tko_run(self._h, int(n))
 
     def state(self) -> np.ndarray:
         out = np.zeros((4, self.Ntheta, self.Nr))
-        _lib().tko_get_state(self._h, _ptr(out))
+        self._lib.tko_get_state(self._h, _ptr(out))
         return out
 
     def replace_state(self, planes4) -> None:
         """Overwrite the state (4 planes), keeping steps and samples."""
         a = np.ascontiguousarray(planes4, dtype=np.float64).reshape(4, self.Ntheta, self.Nr)
-        _lib().tko_replace_state(self._h, _ptr(a))
+        self._lib.tko_replace_state(self._h, _ptr(a))
 
     def coeffs(self):
         """(node, half) coefficient tables, each [NCOEF][Ntheta][Nr]; the half
         table's column a >= 1 holds the values at r*_{a-1/2}."""
         node = np.zeros((NCOEF, self.Ntheta, self.Nr))
         half = np.zeros((NCOEF, self.Ntheta, self.Nr))
-        _lib().tko_get_coeffs(self._h, _ptr(node), _ptr(half))
+        self._lib.tko_get_coeffs(self._h, _ptr(node), _ptr(half))
         return node, half
 
     def waveform(self, obs_id: int) -> np.ndarray:
-        n = _lib().tko_waveform(self._h, obs_id, None, None)
+        n = self._lib.tko_waveform(self._h, obs_id, None, None)
         if n < 0:
             raise ValueError("bad observer id")
         re = np.zeros(max(n, 1))
         im = np.zeros(max(n, 1))
-        _lib().tko_waveform(self._h, obs_id, _ptr(re), _ptr(im))
+        self._lib.tko_waveform(self._h, obs_id, _ptr(re), _ptr(im))
         return (re + 1j * im)[:n]

@@ -32,7 +32,8 @@ EXPORTS = ("tk_make_grid", "tk_precompute_coeffs", "tk_set_initial_data", "tk_ad
            "tk_batch_create", "tk_batch_step", "tk_batch_tune", "tk_batch_set_segment",
            "tk_batch_set_graph_chunk", "tk_batch_info", "tk_batch_last_error", "tk_batch_destroy",
            "tk_extract_noalloc", "tk_adjoint", "tk_set_initial_gaussian", "tk_get_substeps",
-           "tk_set_steps_per_launch", "tk_param_gradient", "tk_check_bounded_wait")
+           "tk_set_steps_per_launch", "tk_param_gradient", "tk_check_bounded_wait",
+           "tk_inject_wait_timeout", "tk_probe_fp64_fma")
 
 
 class TkError(RuntimeError):
@@ -90,6 +91,9 @@ def load_library(path: str = LIB_PATH):
             "tk_param_gradient": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_int,
                                             C.POINTER(C.c_double)]),
             "tk_check_bounded_wait": (C.c_int, [C.c_int, C.c_int, C.c_int64, _ip]),
+            "tk_inject_wait_timeout": (C.c_int, [_vp]),
+            "tk_probe_fp64_fma": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -255,6 +259,19 @@ def tk_check_bounded_wait(n_blocks: int, silent: int, max_polls: int = 1 << 24) 
     _check(None, load_library().tk_check_bounded_wait(int(n_blocks), int(silent), int(max_polls),
                                                       C.byref(t)))
     return bool(t.value)
+
+
+def tk_probe_fp64_fma(blocks_per_sm: int = 4, threads: int = 256, iters: int = 1 << 16):
+    """(seconds, flop) of the FP64 FMA-pipe microbenchmark (tk_probe_fp64_fma)."""
+    s = C.c_double(0.0)
+    f = C.c_double(0.0)
+    _check(None, load_library().tk_probe_fp64_fma(int(blocks_per_sm), int(threads), int(iters),
+                                                  C.byref(s), C.byref(f)))
+    return s.value, f.value
+
+
+def tk_inject_wait_timeout(h) -> None:
+    _check(h, load_library().tk_inject_wait_timeout(h))
 
 
 def tk_steps_done(h) -> int:

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libtk.so")
 SOURCES = ["tk_api.cu", "tk_coeffs.cu", "tk_step.cu", "tk_layout.cu", "tk_batch.cu",
-           "tk_static.cu", "tk_adjoint.cu"]
+           "tk_static.cu", "tk_adjoint.cu", "tk_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -596,7 +596,8 @@ extern "C" tk_status tk_adjoint(tk_solver *S, const double *dL_dwave, const doub
 {
     tk_status st = tkh::enter(S);
     if (st != TK_OK) return st;
-    if (!S->have_state) return tkh::fail(S, TK_ERR_STATE, "tk_adjoint before tk_set_initial_data");
+    st = tkh::need_state(S, "tk_adjoint");
+    if (st != TK_OK) return st;
     if (!grad) return tkh::fail(S, TK_ERR_ARG, "tk_adjoint: grad is NULL");
     if (!dL_dwave && !dL_dfinal)
         return tkh::fail(S, TK_ERR_ARG, "tk_adjoint: give dL_dwave, dL_dfinal or both");
@@ -713,7 +714,7 @@ extern "C" tk_status tk_param_gradient(tk_solver *S, int param, const double *dL
     if (param != 0 && param != 1) return tkh::fail(S, TK_ERR_ARG, "tk_param_gradient: param %d is not 0 (a) or 1 (M)", param);
     if (S->precision != TK_PREC_F64)
         return tkh::fail(S, TK_ERR_ARG, "tk_param_gradient: FP64 solvers only");
-    if (!S->have_state || !S->init_valid)
+    if (!S->have_state || !S->state_valid || !S->init_valid)
         return tkh::fail(S, TK_ERR_STATE, "tk_param_gradient: needs a trajectory from tk_set_initial_data "
                                           "(not restarted with tk_set_state)");
     if (S->nobs == 0) return tkh::fail(S, TK_ERR_ARG, "tk_param_gradient: no observers");

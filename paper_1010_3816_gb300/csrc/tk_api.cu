@@ -47,7 +47,7 @@ void release(tk_solver *S)
     void *ptrs[] = {S->u[0], S->u[1], S->half, S->node, S->b_node, S->w_row,
                     S->x_node, S->x_half, S->ang, S->staging, S->flag, S->stiff, S->ctr, S->wave,
                     S->adj[0], S->adj[1], S->u_init, S->dhalf, S->dnode, S->db_node, S->pflags,
-                    S->obs_scr};
+                    S->obs_scr, S->xbuf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < 2; ++k)
@@ -94,14 +94,26 @@ tk_status enter(tk_solver *S)
     return TK_OK;
 }
 
-// w(theta) of the evolved variable (Phi = w Phi^; 1 for the literal one), as
-// the coefficient precompute writes it to the device for each row.
-static double row_weight(const tk_solver *S, double th)
+tk_status need_state(tk_solver *S, const char *what)
 {
-    if (S->variable == 0) return 1.0;
-    const int s = S->kerr.s, m = S->kerr.m;
-    const double sh = sin(0.5 * th), ch = cos(0.5 * th);
-    return pow(2.0 * sh * sh, 0.5 * fabs((double)(m + s))) * pow(2.0 * ch * ch, 0.5 * fabs((double)(m - s)));
+    if (!S->have_state) return fail(S, TK_ERR_STATE, "%s before tk_set_initial_data", what);
+    if (!S->state_valid)
+        return fail(S, TK_ERR_STATE, "%s: the state is invalid (a persistent launch's bounded wait "
+                                     "ran out); set it again with tk_set_state or tk_set_initial_data",
+                    what);
+    return TK_OK;
+}
+
+tk::WaveRead wave_read(const tk_solver *S, int k)
+{
+    tk::WaveRead r;
+    r.precision = S->precision;
+    r.j0 = S->obs[k].j0;
+    r.ft = S->obs[k].ft;
+    r.wr0 = 1.0 - S->obs[k].fr;
+    r.wr1 = S->obs[k].fr;
+    r.w_row = S->w_row;
+    return r;
 }
 
 void fill_launch(const tk_solver *S, tk::StepLaunch &L)
@@ -123,20 +135,12 @@ void fill_launch(const tk_solver *S, tk::StepLaunch &L)
     L.sample_ctr = S->ctr;
     L.done_ctr = (unsigned int *)(S->ctr + 1);
     L.obs.n = S->nobs;
-    const double dth = M_PI / S->Nth;
     for (int k = 0; k < S->nobs; ++k) {
         L.obs.i0[k] = S->obs[k].i0;
         L.obs.j0[k] = S->obs[k].j0;
         L.obs.wr0[k] = 1.0 - S->obs[k].fr;
         L.obs.wr1[k] = S->obs[k].fr;
         L.obs.ft[k] = S->obs[k].ft;
-        const int j0 = S->obs[k].j0;
-        const double wa = row_weight(S, (j0 + 0.5) * dth), wb = row_weight(S, (j0 + 1.5) * dth);
-        for (int sl = 0; sl < 2; ++sl) {
-            const double wr = sl ? L.obs.wr1[k] : L.obs.wr0[k];
-            L.obs.c0[k][sl] = (float)(wr * (1.0 - S->obs[k].ft) * wa);
-            L.obs.c1[k][sl] = (float)(wr * S->obs[k].ft * wb);
-        }
     }
 }
 
@@ -149,6 +153,7 @@ using tkh::state_elems;
 using tkh::enter;
 using tkh::ensure_wave;
 using tkh::fail;
+using tkh::need_state;
 
 // Tolerated amplification per Lax-Wendroff step of the stiffest angular mode
 // when the solver picks its own number of substeps: a factor e over 40000 steps.
@@ -364,6 +369,7 @@ tk_status tk_set_initial_data(tk_solver *S, const double *phi_re, const double *
         S->init_pi_derived = (pi_re == nullptr);
     }
     S->have_state = true;
+    S->state_valid = true;
     S->count = 0;
     S->steps_done = 0;
     return TK_OK;
@@ -510,7 +516,8 @@ tk_status tk_step(tk_solver *S, int n)
 {
     tk_status st = enter(S);
     if (st != TK_OK) return st;
-    if (!S->have_state) return fail(S, TK_ERR_STATE, "tk_step before tk_set_initial_data");
+    st = need_state(S, "tk_step");
+    if (st != TK_OK) return st;
     if (n < 0) return fail(S, TK_ERR_ARG, "tk_step: n = %d < 0", n);
     if (n == 0) return TK_OK;
     st = ensure_wave(S, S->count + n);
@@ -591,11 +598,24 @@ tk_status tk_step(tk_solver *S, int n)
         int herr = 0;
         TK_CUDA(S, cudaMemcpyAsync(&herr, perr, sizeof(int), cudaMemcpyDeviceToHost, S->stream));
         TK_CUDA(S, cudaStreamSynchronize(S->stream));
-        S->count += n;
-        S->steps_done += n;
-        if (herr)
+        if (S->inject_wait_timeout) {
+            S->inject_wait_timeout = false;
+            herr = 1;
+        }
+        if (herr) {
+            // the samples before this call stay valid: put the device sample
+            // counter back where this call found it and keep the host counts;
+            // the state is invalid until it is set again
+            long long h[2] = {(long long)S->count, 0};
+            TK_CUDA(S, cudaMemcpyAsync(S->ctr, h, sizeof h, cudaMemcpyHostToDevice, S->stream));
+            TK_CUDA(S, cudaStreamSynchronize(S->stream));
+            S->state_valid = false;
+            S->init_valid = false;
             return fail(S, TK_ERR_INTERNAL, "tk_step: a block of the persistent launch waited too long "
                                             "for its neighbours; the state is invalid");
+        }
+        S->count += n;
+        S->steps_done += n;
         return TK_OK;
     }
     const int chunk = graph_chunk(S);
@@ -654,19 +674,37 @@ tk_status tk_extract(tk_solver *S, int obs_id, double *re, double *im, int capac
     const int64_t n = capacity < S->count ? capacity : S->count;
     if (n <= 0) return TK_OK;
     const double *src = S->wave + (size_t)obs_id * S->wave_cap * 4;
+    const tk::WaveRead rd = tkh::wave_read(S, obs_id);
     if (on_device) {
-        TK_CUDA(S, tk::launch_wave_sum(src, n, re, im, S->stream));
+        TK_CUDA(S, tk::launch_wave_sum(src, 0, n, rd, re, im, S->stream));
         return TK_OK;
     }
-    double *tmp = nullptr;
-    st = alloc(S, (void **)&tmp, (size_t)2 * n * sizeof(double));
+    // host read-out through a device buffer the solver keeps (sized to the
+    // waveform buffer's capacity, reallocated only when that grows)
+    if (S->xbuf_cap < S->wave_cap) {
+        if (S->xbuf) {
+            TK_CUDA(S, cudaStreamSynchronize(S->stream));
+            cudaFree(S->xbuf);
+            S->xbuf = nullptr;
+            S->xbuf_cap = 0;
+        }
+        st = alloc(S, (void **)&S->xbuf, (size_t)2 * S->wave_cap * sizeof(double));
+        if (st != TK_OK) return st;
+        S->xbuf_cap = S->wave_cap;
+    }
+    double *tmp = S->xbuf;
+    TK_CUDA(S, tk::launch_wave_sum(src, 0, n, rd, tmp, tmp + n, S->stream));
+    TK_CUDA(S, cudaMemcpyAsync(re, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, S->stream));
+    TK_CUDA(S, cudaMemcpyAsync(im, tmp + n, n * sizeof(double), cudaMemcpyDeviceToHost, S->stream));
+    TK_CUDA(S, cudaStreamSynchronize(S->stream));
+    return TK_OK;
+}
+
+tk_status tk_inject_wait_timeout(tk_solver *S)
+{
+    tk_status st = enter(S);
     if (st != TK_OK) return st;
-    cudaError_t e = tk::launch_wave_sum(src, n, tmp, tmp + n, S->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(re, tmp, n * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(im, tmp + n, n * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
-    cudaFree(tmp);
-    if (e != cudaSuccess) return fail(S, TK_ERR_CUDA, "tk_extract: %s", cudaGetErrorString(e));
+    S->inject_wait_timeout = true;
     return TK_OK;
 }
 
@@ -674,7 +712,8 @@ tk_status tk_get_state(tk_solver *S, double *planes4, int on_device)
 {
     tk_status st = enter(S);
     if (st != TK_OK) return st;
-    if (!S->have_state) return fail(S, TK_ERR_STATE, "tk_get_state before tk_set_initial_data");
+    st = need_state(S, "tk_get_state");
+    if (st != TK_OK) return st;
     if (!planes4) return fail(S, TK_ERR_ARG, "tk_get_state: planes4 is NULL");
     if (on_device) {
         TK_CUDA(S, tk::launch_export_state(S->precision, S->Nr, S->Nth, S->NP, S->u[S->cur], planes4,
@@ -699,7 +738,9 @@ tk_status tk_set_state(tk_solver *S, const double *planes4, int on_device)
     if (!planes4) return fail(S, TK_ERR_ARG, "tk_set_state: planes4 is NULL");
     const size_t plane = (size_t)S->Nth * S->Nr;
     S->init_valid = false;   // the trajectory no longer starts from the stored u^0
-    return import_planes(S, planes4, planes4 + plane, planes4 + 2 * plane, planes4 + 3 * plane, on_device);
+    st = import_planes(S, planes4, planes4 + plane, planes4 + 2 * plane, planes4 + 3 * plane, on_device);
+    if (st == TK_OK) S->state_valid = true;
+    return st;
 }
 
 tk_status tk_stability_bound(tk_solver *S, double growth_per_step, double *dt_max,
@@ -741,7 +782,8 @@ tk_status tk_check_finite(tk_solver *S)
 {
     tk_status st = enter(S);
     if (st != TK_OK) return st;
-    if (!S->have_state) return fail(S, TK_ERR_STATE, "tk_check_finite before tk_set_initial_data");
+    st = need_state(S, "tk_check_finite");
+    if (st != TK_OK) return st;
     int h = 0;
     TK_CUDA(S, cudaMemsetAsync(S->flag, 0, sizeof(int), S->stream));
     TK_CUDA(S, tk::launch_finite_check(S->precision, state_elems(S), S->u[S->cur], S->flag, S->stream));

@@ -327,8 +327,8 @@ tk_status advance_members(tk_batch *B, int n)
 tk_status check_members(tk_batch *B)
 {
     for (tk_solver *S : B->mem)
-        if (!S->have_state)
-            return bfail(B, TK_ERR_STATE, "tk_batch: a member has no initial data");
+        if (!S->have_state || !S->state_valid)
+            return bfail(B, TK_ERR_STATE, "tk_batch: a member has no valid state");
     return TK_OK;
 }
 

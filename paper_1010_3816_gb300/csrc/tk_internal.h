@@ -57,9 +57,22 @@ struct ObsDev {
     double wr0[kMaxObservers];      // 1 - fr
     double wr1[kMaxObservers];      // fr
     double ft[kMaxObservers];       // theta weight fth
-    // FP32 sweeps: the sample's weights of rows j0 and j0 + 1 for slot 0 and 1,
-    // wr_slot * (1 - fth) * w(theta_j0) and wr_slot * fth * w(theta_j0+1)
-    float c0[kMaxObservers][2], c1[kMaxObservers][2];
+};
+
+// How the read-out forms an observer's samples from its buffer entries.  An
+// entry is 4 doubles per outer step.  FP64 solvers store two weighted partial
+// sums (slot 0 from column i0, slot 1 from column i0 + 1) as (re, im) pairs
+// and the sample is slot 0 + slot 1.  FP32 solvers store the FP32 values
+// themselves, 8 floats: for slot s, Phi_R and Phi_I at rows j0 and j0 + 1
+// (floats 4s .. 4s + 3 = R_j0, I_j0, R_j0+1, I_j0+1); the read-out converts
+// them to FP64 (exactly) and forms the same bilinear sample as the FP64 path,
+// in FP64.
+struct WaveRead {
+    int precision;
+    int j0;                 // lower theta row
+    double ft;              // theta weight fth
+    double wr0, wr1;        // 1 - fr, fr
+    const double *w_row;    // w(theta_j) on the device
 };
 
 // ---- coefficient precompute (tk_coeffs.cu) ----
@@ -86,8 +99,10 @@ cudaError_t launch_gaussian(int Nr, int Ntheta, double rs_min, double drs, doubl
                             double *re, double *im, cudaStream_t st);
 cudaError_t launch_finite_check(int precision, size_t n, const void *u, int *flag,
                                 cudaStream_t st);
-cudaError_t launch_wave_sum(const double *wave_obs, int64_t count, double *re, double *im,
-                            cudaStream_t st);
+// Samples [first, first + count) of one observer's buffer to re[0..count),
+// im[0..count) (device pointers).
+cudaError_t launch_wave_sum(const double *wave_obs, int64_t first, int64_t count, const WaveRead &r,
+                            double *re, double *im, cudaStream_t st);
 
 // ---- time step (tk_step.cu) ----
 struct StepLaunch {

@@ -62,13 +62,38 @@ __global__ void finite_kernel(size_t n, const T *__restrict__ u, int *flag)
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
-__global__ void wave_sum_kernel(const double *__restrict__ w, int64_t count, double *__restrict__ re,
-                                double *__restrict__ im)
+// Waveform read-out (the bilinear sample of Phi = w Phi^ in r* and theta).
+// FP64 entries are two weighted partial sums: the sample is their sum.  FP32
+// entries are the state values of the interpolation cell (WaveRead): the
+// sample is formed here in FP64 by the FP64 path's own expression,
+//   slot s = wr_s [(1 - fth) w_j0 Phi_{s,j0} + fth w_j0+1 Phi_{s,j0+1}],
+// on the exactly converted values.
+__global__ void wave_sum_kernel(const double *__restrict__ w, int64_t first, int64_t count,
+                                const WaveRead r, double *__restrict__ re, double *__restrict__ im)
 {
     const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (n >= count) return;
-    re[n] = w[4 * n + 0] + w[4 * n + 2];
-    im[n] = w[4 * n + 1] + w[4 * n + 3];
+    const double *p = w + 4 * (first + n);
+    if (r.precision == 0) {
+        re[n] = p[0] + p[2];
+        im[n] = p[1] + p[3];
+        return;
+    }
+    const float4 *f = reinterpret_cast<const float4 *>(p);
+    const double w0 = (1.0 - r.ft) * r.w_row[r.j0];
+    const double w1 = r.ft * r.w_row[r.j0 + 1];
+    double sr[2], si[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const float4 v = f[s];   // Phi_R, Phi_I at row j0, then at row j0 + 1
+        const double cr = w0 * (double)v.x + w1 * (double)v.z;
+        const double ci = w0 * (double)v.y + w1 * (double)v.w;
+        const double wr = s ? r.wr1 : r.wr0;
+        sr[s] = wr * cr;
+        si[s] = wr * ci;
+    }
+    re[n] = sr[0] + sr[1];
+    im[n] = si[0] + si[1];
 }
 
 // SplitMix64 (G. L. Steele, D. Lea, C. H. Flood, "Fast splittable
@@ -155,13 +180,13 @@ cudaError_t launch_finite_check(int precision, size_t n, const void *u, int *fla
     return cudaGetLastError();
 }
 
-cudaError_t launch_wave_sum(const double *wave_obs, int64_t count, double *re, double *im,
-                            cudaStream_t st)
+cudaError_t launch_wave_sum(const double *wave_obs, int64_t first, int64_t count, const WaveRead &r,
+                            double *re, double *im, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
     const int threads = 256;
     const int64_t blocks = (count + threads - 1) / threads;
-    wave_sum_kernel<<<(unsigned)blocks, threads, 0, st>>>(wave_obs, count, re, im);
+    wave_sum_kernel<<<(unsigned)blocks, threads, 0, st>>>(wave_obs, first, count, r, re, im);
     return cudaGetLastError();
 }
 

@@ -34,6 +34,10 @@ struct tk_solver {
     // physics
     tk::Kerr kerr{};
     bool have_coeffs = false, have_state = false;
+    // false after a persistent launch's bounded wait ran out: the state is
+    // then invalid until tk_set_initial_data or tk_set_state replaces it
+    bool state_valid = true;
+    bool inject_wait_timeout = false;   // tk_inject_wait_timeout (host-side test hook)
     // observers and waveform samples
     struct Obs {
         double rs, th;
@@ -43,6 +47,8 @@ struct tk_solver {
     int nobs = 0;
     double *wave = nullptr;  // [obs][cap][2 slots][re, im]
     int64_t wave_cap = 0;
+    double *xbuf = nullptr;  // tk_extract's device buffer for host read-outs (2 * xbuf_cap)
+    int64_t xbuf_cap = 0;
     int64_t count = 0;
     int64_t steps_done = 0;
     // launch shape
@@ -79,6 +85,11 @@ tk_status alloc(tk_solver *S, void **p, size_t bytes);
 tk_status ensure_wave(tk_solver *S, int64_t need);
 tk_status enter(tk_solver *S);
 void fill_launch(const tk_solver *S, tk::StepLaunch &L);
+// How observer k's samples are read out of the waveform buffer.
+tk::WaveRead wave_read(const tk_solver *S, int k);
+// TK_ERR_STATE unless the solver holds a valid state (initial data set, and
+// no persistent launch failed since); `what` names the call.
+tk_status need_state(tk_solver *S, const char *what);
 
 }  // namespace tkh
 

@@ -1,16 +1,15 @@
 // tk_static.cu -- tk_extract_noalloc: reading a waveform into host memory
 // without any device allocation.
 //
-// tk_extract with a host destination sums the two partial samples of every
-// step into a temporary device buffer that it allocates with cudaMalloc on
-// each call.  Callers that must not allocate device memory -- code running
-// while another thread captures a CUDA graph, real-time loops whose memory
-// budget is fixed up front, or hosts that route all device memory through
-// their own pool -- use this variant instead: the same summing kernel writes
-// into a fixed array compiled into the library, and the result is copied from
-// there to the caller's host buffers.
-#include <mutex>
-
+// tk_extract with a host destination forms the samples in a device buffer
+// that the solver allocates on first use and again whenever the waveform
+// buffer grows.  Some callers must not allocate device memory at all once
+// they are set up: hosts that hand all device memory to their own pool and
+// treat any other cudaMalloc as a failure, and loops whose device-memory
+// budget is fixed up front (a cudaMalloc there can also synchronize the
+// device and stall other streams).  They use this variant instead: the same
+// read-out kernel writes into a fixed array compiled into the library, and
+// the result is copied from there to the caller's host buffers.
 #include "tk_solver_impl.h"
 
 namespace {
@@ -24,36 +23,18 @@ constexpr int kMaxNoallocSamples = 65536;
 // writes every element it then reads, so nothing has to start at zero.
 static __device__ __align__(256) double g_noalloc_scratch[2 * kMaxNoallocSamples];
 
-// Device address of g_noalloc_scratch, looked up once per device.
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double *g_scratch_ptr[kMaxDevices] = {nullptr};
-
-__global__ void wave_sum_into_kernel(const double *__restrict__ w, long long first, int count,
-                                     double *__restrict__ out)
-{
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= count) return;
-    const double *p = w + 4 * (first + n);
-    out[n] = p[0] + p[2];
-    out[count + n] = p[1] + p[3];
-}
-
-// With the solver's device current: the scratch's device address on it.
+// With the solver's device current: the scratch's device address on it.  The
+// address is looked up on every call (after the first call on a device this
+// is a table lookup): a cached pointer would go stale if the program reset
+// the device and the module were loaded again at another address.
 tk_status scratch_for(tk_solver *S, double **ptr)
 {
-    if (S->device < 0 || S->device >= kMaxDevices)
-        return tkh::fail(S, TK_ERR_ARG, "tk_extract_noalloc: device %d not supported", S->device);
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[S->device]) {
-        double *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return tkh::fail(S, TK_ERR_CUDA, "tk_extract_noalloc: cudaGetSymbolAddress: %s",
-                             cudaGetErrorString(e));
-        g_scratch_ptr[S->device] = p;
-    }
-    *ptr = g_scratch_ptr[S->device];
+    double *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return tkh::fail(S, TK_ERR_CUDA, "tk_extract_noalloc: cudaGetSymbolAddress: %s",
+                         cudaGetErrorString(e));
+    *ptr = p;
     return TK_OK;
 }
 
@@ -80,10 +61,8 @@ extern "C" tk_status tk_extract_noalloc(tk_solver *S, int obs_id, int first, int
     st = scratch_for(S, &scratch);
     if (st != TK_OK) return st;
     const double *src = S->wave + (size_t)obs_id * S->wave_cap * 4;
-    const int threads = 256;
-    wave_sum_into_kernel<<<(count + threads - 1) / threads, threads, 0, S->stream>>>(src, first, count,
-                                                                                   scratch);
-    TK_CUDA(S, cudaGetLastError());
+    TK_CUDA(S, tk::launch_wave_sum(src, first, count, tkh::wave_read(S, obs_id), scratch,
+                                   scratch + count, S->stream));
     TK_CUDA(S, cudaMemcpyAsync(re, scratch, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost,
                                S->stream));
     TK_CUDA(S, cudaMemcpyAsync(im, scratch + count, (size_t)count * sizeof(double),

@@ -287,9 +287,12 @@ __device__ __forceinline__ void full_node(const T (&hm)[4][K], const T (&hp)[4][
     }
 }
 
-// Partial bilinear sample (Sec. "waveform extraction" of the design notes):
-// slot 0 holds (1 - fr) * [(1-fth) w_j0 Phi_{i0,j0} + fth w_j0+1 Phi_{i0,j0+1}],
+// Partial bilinear sample (the paper prints no extraction rule; the sample
+// is the bilinear interpolant in (r*, theta) of the physical Phi = w Phi^):
+// in FP64, slot 0 holds (1 - fr) * [(1-fth) w_j0 Phi_{i0,j0} + fth w_j0+1 Phi_{i0,j0+1}],
 // slot 1 the same at column i0 + 1 times fr; the sample is slot 0 + slot 1.
+// In FP32 a slot holds the four FP32 values Phi_{R,I} at rows j0, j0 + 1, and
+// the read-out forms the same sample from them in FP64 (WaveRead).
 // observe_one: observer k's slot from the column's Phi_R, Phi_I (K rows per
 // lane); all 32 lanes take part, lane 0 writes.
 template <typename T, int K>
@@ -324,10 +327,9 @@ __device__ __forceinline__ void observe_one(int lane, int k, int slot, const T (
         const long long sample = *(volatile const long long *)sample_ctr + sample_offset;
         double *dst = wave + ((size_t)k * cap + sample) * 4 + 2 * slot;
         if constexpr (sizeof(T) == 4) {
-            // FP32: the weights precomputed on the host, FP32 arithmetic
-            const float c0 = obs.c0[k][slot], c1 = obs.c1[k][slot];
-            dst[0] = (double)fmaf(c1, br, c0 * ar);
-            dst[1] = (double)fmaf(c1, bi, c0 * ai);
+            // FP32: the values themselves, one 16-byte store, no arithmetic
+            // (the entry is 16-byte aligned: 4 doubles per sample, 2 per slot)
+            *reinterpret_cast<float4 *>(dst) = make_float4(ar, ai, br, bi);
         } else {
             const double w0 = (1.0 - obs.ft[k]) * w_row[j0];
             const double w1 = obs.ft[k] * w_row[j0 + 1];

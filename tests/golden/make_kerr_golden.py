@@ -3,12 +3,18 @@ the Kerr a = 0.9, 25601 x 64, 38400-outer-step workload (two Lax-Wendroff
 steps per outer step).  Calls only oracle/ and the shared input generator.
 
 Stored: both waveforms (every sample), the physical state Phi = w Phi^,
-Pi = w Pi^ on every 8th theta row and every 16th r* column, and the L2 norm of
+Pi = w Pi^ on every theta row and every 4th r* column, and the L2 norm of
 each full physical plane.  Takes about two hours on 6 cores.
+
+With --fma it writes kerr_25601x64_oracle_fma.npz: the same run through the
+same oracle source compiled with FMA contraction (oracle.Solver(build="fma")),
+a second correct rounding order of the scheme.
 
 With --perturbed it writes kerr_25601x64_oracle_perturbed.npz instead: the same
 run from the real initial plane times 1 + 2.2e-16 * N(0, 1) (numpy's default
-generator, seed 12345), i.e. a change of about one ulp.  With --noisy it writes
+generator, seed 12345), i.e. a change of about one ulp.  The perturbed and
+noisy runs store the state on every 8th theta row and every 16th r* column
+only.  With --noisy it writes
 kerr_25601x64_oracle_noisy.npz: the run with every value of the state
 multiplied by 1 + 8.8e-16 * N(0, 1) after every 16th outer step (seed 12346),
 a random walk of about one ulp per outer step, the size of the rounding
@@ -16,7 +22,7 @@ differences two correct implementations accumulate.  The differences of these
 runs from the plain one are the run's own conditioning, which sets the parity
 bar of the full-length test.
 
-    python tests/golden/make_kerr_golden.py [threads] [--perturbed | --noisy]
+    python tests/golden/make_kerr_golden.py [threads] [--perturbed | --noisy | --fma]
 """
 import math
 import os
@@ -32,8 +38,10 @@ import numpy as np  # noqa: E402
 import oracle  # noqa: E402
 from inputs import KERR_25601x64, initial_planes  # noqa: E402
 
-ROWS = slice(0, None, 8)
-COLS = slice(0, None, 16)
+ROWS = slice(0, None, 1)
+COLS = slice(0, None, 4)
+SPARSE_ROWS = slice(0, None, 8)      # the perturbed and noisy runs
+SPARSE_COLS = slice(0, None, 16)
 
 
 EPS = 2.2e-16
@@ -46,11 +54,15 @@ def main():
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
     perturbed = "--perturbed" in sys.argv
     noisy = "--noisy" in sys.argv
+    fma = "--fma" in sys.argv
+    assert perturbed + noisy + fma <= 1, "one variant at a time"
+    rows, cols = (SPARSE_ROWS, SPARSE_COLS) if (perturbed or noisy) else (ROWS, COLS)
     if args:
         oracle.set_threads(int(args[0]))
     w = KERR_25601x64
     sol = oracle.Solver(M=w.M, a=w.a, s=w.s, m=w.m, rs_min=w.rs_min, rs_max=w.rs_max, Nr=w.Nr,
-                        Ntheta=w.Ntheta, dt=w.dt, substeps=w.substeps, variable=w.variable)
+                        Ntheta=w.Ntheta, dt=w.dt, substeps=w.substeps, variable=w.variable,
+                        build="fma" if fma else "plain")
     ids = [sol.add_observer(r, t) for r, t in w.observers]
     re, im = initial_planes(w)
     if perturbed:
@@ -75,14 +87,15 @@ def main():
     phys = st * wt
     np.savez_compressed(
         os.path.join(HERE, "kerr_25601x64_oracle" + ("_perturbed" if perturbed else "")
-                     + ("_noisy" if noisy else "") + ".npz"),
+                     + ("_noisy" if noisy else "") + ("_fma" if fma else "") + ".npz"),
         wave0=sol.waveform(ids[0]), wave1=sol.waveform(ids[1]),
-        state_sub=phys[:, ROWS, COLS], plane_norms=np.linalg.norm(phys.reshape(4, -1), axis=1),
-        rows=np.arange(w.Ntheta)[ROWS], cols=np.arange(w.Nr)[COLS],
+        state_sub=phys[:, rows, cols], plane_norms=np.linalg.norm(phys.reshape(4, -1), axis=1),
+        rows=np.arange(w.Ntheta)[rows], cols=np.arange(w.Nr)[cols],
         note=np.array("oracle full run of " + w.name + f", {w.substeps} LW steps per outer step"
                       + (f", real initial plane times 1 + {EPS} N(0,1), seed {SEED}" if perturbed else "")
                       + (f", state times 1 + {NOISE_EPS} N(0,1) every {NOISE_EVERY} outer steps, seed "
-                         f"{SEED + 1}" if noisy else "")))
+                         f"{SEED + 1}" if noisy else "")
+                      + (", oracle compiled with FMA contraction" if fma else "")))
 
 
 if __name__ == "__main__":

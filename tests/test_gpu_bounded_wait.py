@@ -68,3 +68,50 @@ def test_argument_errors():
     for args in ((1, 0), (65, 0), (8, 8), (8, -2)):
         with pytest.raises(tk.TkError):
             tk.tk_check_bounded_wait(*args)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_timed_out_step_invalidates_the_state_until_it_is_set_again(precision):
+    """A persistent launch whose waits ran out (injected on the host after the
+    launch ran normally) leaves the step and sample counts where the call
+    found them and the samples taken before it readable; every call that
+    would read the state refuses (TK_ERR_STATE) until tk_set_state sets it
+    again, and stepping on from the restored state gives the bits of the
+    uninterrupted run."""
+    import paper_1010_3816_gb300 as tk
+    w = Workload(name="bw2", a=0.7, m=2, rs_min=-30.0, rs_max=70.0, Nr=1601, Ntheta=32, dt=1 / 32,
+                 substeps=2, center=5.0, width=3.0, noise=1e-3, seed=8,
+                 observers=((10.0, math.pi / 2),))
+
+    def solver():
+        g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
+                      substeps=w.substeps, precision=precision)
+        g.precompute(w.a, w.M, w.s, w.m)
+        g.set_steps_per_launch(-1)
+        g.set_initial(*initial_planes(w))
+        return g, g.add_observer(*w.observers[0])
+
+    ref, kr = solver()
+    ref.step(30)
+    ref.step(30)
+    want_state, want_wave = ref.state(), ref.waveform(kr)
+    ref.close()
+
+    g, k = solver()
+    g.step(30)
+    checkpoint, wave30 = g.state(), g.waveform(k)
+    tk.tk_inject_wait_timeout(g.h)
+    with pytest.raises(tk.TkError) as e:
+        g.step(30)
+    assert e.value.status == tk.TK_ERR_INTERNAL
+    assert tk.tk_steps_done(g.h) == 30
+    assert np.array_equal(g.waveform(k), wave30)
+    for call in (lambda: g.step(1), g.state, lambda: tk.tk_check_finite(g.h)):
+        with pytest.raises(tk.TkError) as e:
+            call()
+        assert e.value.status == tk.TK_ERR_STATE
+    tk.tk_set_state(g.h, checkpoint)
+    g.step(30)
+    assert np.array_equal(g.state(), want_state)
+    assert np.array_equal(g.waveform(k), want_wave)
+    g.close()

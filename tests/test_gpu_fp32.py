@@ -1,9 +1,8 @@
 """FP32 step (TK_PREC_F32): FP32 planes, tables and stencil arithmetic, with
 the coefficient precompute (including the r(r*) inversion) in FP64 and the
-waveform samples formed in FP32 from weights precomputed in FP64 on the host
-(stored as FP64).  Its error against the FP64 oracle is measured and bounded
-per waveform; the bounds below are the measured errors with a safety factor,
-not parity claims.
+waveform samples formed in FP64 from the FP32 state values.  Its error against
+the FP64 oracle is measured and bounded per waveform; the bounds below are the
+measured errors with a safety factor, not parity claims.
 """
 import math
 
@@ -55,3 +54,29 @@ def test_fp32_kerr_25601x64_full_run_error():
     errs = [rel_l2(a, b) for a, b in zip(g32[1], g64[1])]
     print("FP32 vs FP64 waveform relative L2 per observer:", errs)
     assert all(np.isfinite(errs)) and max(errs) < 1e-2
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(Ntheta=128, Nr=401, substeps=4), dict(variable=0, dt=0.01, m=3)])
+def test_fp32_samples_are_formed_in_fp64(kw):
+    """The last sample of every observer equals the bilinear interpolant of the
+    final FP32 state (exported exactly as doubles) evaluated in FP64 with the
+    oracle's row weights, to FP64 rounding: the FP32 variant keeps FP64 for the
+    waveform, only its state is FP32."""
+    import oracle
+    w = BASE.with_(**kw)
+    gs, gw = run_gpu(w, precision=1)
+    assert np.array_equal(gs, gs.astype(np.float32).astype(np.float64))   # FP32 state
+    th = (np.arange(w.Ntheta) + 0.5) * (math.pi / w.Ntheta)
+    for (rs, tho), wave in zip(w.observers, gw):
+        fi = (rs - w.rs_min) / w.drs
+        fj = tho / (math.pi / w.Ntheta) - 0.5
+        i0, j0 = min(int(fi), w.Nr - 2), min(int(fj), w.Ntheta - 2)
+        fr, ft = fi - i0, fj - j0
+        wa = oracle.weight(w.s, w.m, w.variable, th[j0])
+        wb = oracle.weight(w.s, w.m, w.variable, th[j0 + 1])
+        want = 0.0
+        for dc, wr in ((0, 1.0 - fr), (1, fr)):
+            col = gs[0][:, i0 + dc] + 1j * gs[1][:, i0 + dc]
+            want += wr * ((1.0 - ft) * wa * col[j0] + ft * wb * col[j0 + 1])
+        got = wave[-1]
+        assert abs(got - want) <= 1e-14 * abs(want), (got, want)
