@@ -182,6 +182,19 @@ __device__ __forceinline__ void warp_range(int Nr, int wib, int *i0, int *i1, in
     *left = prev;
 }
 
+// FP32 with an even number of rows per lane: the rows go in pairs through
+// GB300's packed FP32 instructions (__ffma2_rn, __fadd2_rn, __fmul2_rn: two
+// single-precision operations per instruction, each rounded exactly like the
+// scalar one), so the node routines below are bit-identical to their scalar
+// form with half as many FP32 arithmetic instructions.
+__device__ __forceinline__ float2 pr2(const float *v, int t) { return make_float2(v[t], v[t + 1]); }
+__device__ __forceinline__ float2 ng2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ void st2(float *v, int t, float2 x)
+{
+    v[t] = x.x;
+    v[t + 1] = x.y;
+}
+
 // Eq. (lw1): u^{n+1/2}_{i+1/2} from a = u^n_i and c = u^n_{i+1}.  The Phi
 // components come out divided by eh = dt/4: the table entries HP, HQ carry the
 // factor 1/eh and the node tables multiply the half-node Phi values back by
@@ -195,16 +208,65 @@ __device__ __forceinline__ void half_node(const T (&a)[4][K], const T (&c)[4][K]
     constexpr int NP = 32 * K;
     const FmaK<T> k1 = fma_k<T>();
     T sR[K], sI[K], upR[K], upI[K], dnR[K], dnI[K];
+    if constexpr (sizeof(T) == 4 && K % 2 == 0) {
 #pragma unroll
-    for (int t = 0; t < K; ++t) {
-        sR[t] = fma(a[0][t], k1.one, c[0][t]);
-        sI[t] = fma(a[1][t], k1.one, c[1][t]);
+        for (int t = 0; t < K; t += 2) {
+            st2(sR, t, __fadd2_rn(pr2(a[0], t), pr2(c[0], t)));
+            st2(sI, t, __fadd2_rn(pr2(a[1], t), pr2(c[1], t)));
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            sR[t] = fma(a[0][t], k1.one, c[0][t]);
+            sI[t] = fma(a[1][t], k1.one, c[1][t]);
+        }
     }
     theta_neighbours<T, K>(sR, upR, dnR);
     theta_neighbours<T, K>(sI, upI, dnI);
     T q[kNCH][K];
 #pragma unroll
     for (int k = 0; k < kNCH; ++k) ldk<T, K>(tab + k * NP, q[k]);
+    if constexpr (sizeof(T) == 4 && K % 2 == 0) {
+#pragma unroll
+        for (int t = 0; t < K; t += 2) {
+            const float2 a0 = pr2(a[0], t), a1 = pr2(a[1], t), a2 = pr2(a[2], t), a3 = pr2(a[3], t);
+            const float2 c0 = pr2(c[0], t), c1 = pr2(c[1], t), c2 = pr2(c[2], t), c3 = pr2(c[3], t);
+            const float2 sPR = __fadd2_rn(a2, c2);
+            const float2 sPI = __fadd2_rn(a3, c3);
+            const float2 HP = pr2(q[H_HP], t), HQ = pr2(q[H_HQ], t), PAR = pr2(q[H_PAR], t);
+            const float2 PCR = pr2(q[H_PCR], t), PI = pr2(q[H_PI], t), FAR = pr2(q[H_FAR], t);
+            const float2 FAI = pr2(q[H_FAI], t), FCR = pr2(q[H_FCR], t), FCI = pr2(q[H_FCI], t);
+            const float2 KP = pr2(q[H_KP], t), KM = pr2(q[H_KM], t);
+            if constexpr (PI_TERM) {
+                st2(h[0], t, __ffma2_rn(HQ, c0, __ffma2_rn(HP, a0, sPR)));
+                st2(h[1], t, __ffma2_rn(HQ, c1, __ffma2_rn(HP, a1, sPI)));
+            } else {
+                st2(h[0], t, __ffma2_rn(HQ, c0, __fmul2_rn(HP, a0)));
+                st2(h[1], t, __ffma2_rn(HQ, c1, __fmul2_rn(HP, a1)));
+            }
+            float2 x = __fmul2_rn(PAR, a2);
+            x = __ffma2_rn(PCR, c2, x);
+            x = __ffma2_rn(ng2(PI), sPI, x);
+            x = __ffma2_rn(FAR, a0, x);
+            x = __ffma2_rn(ng2(FAI), a1, x);
+            x = __ffma2_rn(FCR, c0, x);
+            x = __ffma2_rn(ng2(FCI), c1, x);
+            x = __ffma2_rn(KP, pr2(upR, t), x);
+            x = __ffma2_rn(KM, pr2(dnR, t), x);
+            st2(h[2], t, x);
+            float2 y = __fmul2_rn(PAR, a3);
+            y = __ffma2_rn(PCR, c3, y);
+            y = __ffma2_rn(PI, sPR, y);
+            y = __ffma2_rn(FAR, a1, y);
+            y = __ffma2_rn(FAI, a0, y);
+            y = __ffma2_rn(FCR, c1, y);
+            y = __ffma2_rn(FCI, c0, y);
+            y = __ffma2_rn(KP, pr2(upI, t), y);
+            y = __ffma2_rn(KM, pr2(dnI, t), y);
+            st2(h[3], t, y);
+        }
+        return;
+    }
 #pragma unroll
     for (int t = 0; t < K; ++t) {
         const T sPR = fma(a[2][t], k1.one, c[2][t]);
@@ -248,16 +310,61 @@ __device__ __forceinline__ void full_node(const T (&hm)[4][K], const T (&hp)[4][
     constexpr int NP = 32 * K;
     const FmaK<T> k1 = fma_k<T>();
     T sR[K], sI[K], upR[K], upI[K], dnR[K], dnI[K];
+    if constexpr (sizeof(T) == 4 && K % 2 == 0) {
 #pragma unroll
-    for (int t = 0; t < K; ++t) {
-        sR[t] = fma(hp[0][t], k1.one, hm[0][t]);
-        sI[t] = fma(hp[1][t], k1.one, hm[1][t]);
+        for (int t = 0; t < K; t += 2) {
+            st2(sR, t, __fadd2_rn(pr2(hp[0], t), pr2(hm[0], t)));
+            st2(sI, t, __fadd2_rn(pr2(hp[1], t), pr2(hm[1], t)));
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            sR[t] = fma(hp[0][t], k1.one, hm[0][t]);
+            sI[t] = fma(hp[1][t], k1.one, hm[1][t]);
+        }
     }
     theta_neighbours<T, K>(sR, upR, dnR);
     theta_neighbours<T, K>(sI, upI, dnI);
     T q[kNCN][K];
 #pragma unroll
     for (int k = 0; k < kNCN; ++k) ldk<T, K>(tab + k * NP, q[k]);
+    if constexpr (sizeof(T) == 4 && K % 2 == 0) {
+        const float2 e2 = make_float2(e, e);
+#pragma unroll
+        for (int t = 0; t < K; t += 2) {
+            const float2 m0 = pr2(hm[0], t), m1 = pr2(hm[1], t), m2 = pr2(hm[2], t), m3 = pr2(hm[3], t);
+            const float2 p0 = pr2(hp[0], t), p1 = pr2(hp[1], t), p2 = pr2(hp[2], t), p3 = pr2(hp[3], t);
+            const float2 sPR = __fadd2_rn(p2, m2);
+            const float2 sPI = __fadd2_rn(p3, m3);
+            const float2 B = pr2(q[N_B], t), PPR = pr2(q[N_PPR], t), PMR = pr2(q[N_PMR], t);
+            const float2 C2I = pr2(q[N_C2I], t), FPR = pr2(q[N_FPR], t), FPI = pr2(q[N_FPI], t);
+            const float2 FMR = pr2(q[N_FMR], t), FMI = pr2(q[N_FMI], t);
+            const float2 KP = pr2(q[N_KP], t), KM = pr2(q[N_KM], t);
+            st2(o[0], t, __ffma2_rn(e2, sPR, __ffma2_rn(B, m0, __ffma2_rn(ng2(B), p0, pr2(u[0], t)))));
+            st2(o[1], t, __ffma2_rn(e2, sPI, __ffma2_rn(B, m1, __ffma2_rn(ng2(B), p1, pr2(u[1], t)))));
+            float2 x = __ffma2_rn(PPR, p2, pr2(u[2], t));
+            x = __ffma2_rn(PMR, m2, x);
+            x = __ffma2_rn(ng2(C2I), sPI, x);
+            x = __ffma2_rn(FPR, p0, x);
+            x = __ffma2_rn(ng2(FPI), p1, x);
+            x = __ffma2_rn(FMR, m0, x);
+            x = __ffma2_rn(ng2(FMI), m1, x);
+            x = __ffma2_rn(KP, pr2(upR, t), x);
+            x = __ffma2_rn(KM, pr2(dnR, t), x);
+            st2(o[2], t, x);
+            float2 y = __ffma2_rn(PPR, p3, pr2(u[3], t));
+            y = __ffma2_rn(PMR, m3, y);
+            y = __ffma2_rn(C2I, sPR, y);
+            y = __ffma2_rn(FPR, p1, y);
+            y = __ffma2_rn(FPI, p0, y);
+            y = __ffma2_rn(FMR, m1, y);
+            y = __ffma2_rn(FMI, m0, y);
+            y = __ffma2_rn(KP, pr2(upI, t), y);
+            y = __ffma2_rn(KM, pr2(dnI, t), y);
+            st2(o[3], t, y);
+        }
+        return;
+    }
 #pragma unroll
     for (int t = 0; t < K; ++t) {
         const T sPR = fma(hp[2][t], k1.one, hm[2][t]);

@@ -407,6 +407,65 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// Bulk copies (the TMA unit's cp.async.bulk) of a column's tables into a
+// warp's shared-memory ring: one thread issues the two copies of a column
+// (half-node and node tables, contiguous in global memory), which complete on
+// the mbarrier of their ring slot; the warp waits on that mbarrier's phase
+// before reading the slot.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_fetch(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Polls of a ring slot's mbarrier before the wait gives up (each try_wait
+// itself suspends the warp for a while); a copy of valid memory completes
+// long before.
+constexpr long long kMaxMbarPolls = 1ll << 22;
+
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    for (long long i = 0; i < kMaxMbarPolls; ++i)
+        if (mbar_test(bar, parity)) return true;
+    return false;
+}
+
+// The ring's per-warp state across sweeps: the slot of the next copy (also
+// the slot the next wait is for), and per slot the parity of the next phase
+// to wait for and of the copies issued.
+struct RingState {
+    int cur;
+    unsigned wait_ph, issue_ph;
+};
+
 // Issue the copies of the first-level tables of sweep step p (half_{p-1},
 // node_{p-1}) into `slot`, then commit a group (empty where the column is
 // outside the grid).
@@ -572,9 +631,51 @@ constexpr int multi_warps()
 }
 
 template <typename T, int K, int W, int LV>
-constexpr size_t multi_smem_bytes()
+__host__ __device__ constexpr size_t multi_ring_bytes()
 {
     return (size_t)W * (LV + 1) * kSlotCols * 32 * K * sizeof(T);
+}
+
+// the rings, then one mbarrier per ring slot
+template <typename T, int K, int W, int LV>
+constexpr size_t multi_smem_bytes()
+{
+    return multi_ring_bytes<T, K, W, LV>() + (size_t)W * (LV + 1) * sizeof(unsigned long long);
+}
+
+// Bulk copy of the tables of sweep position p (half_{p-1}, node_{p-1}; the
+// column clamped into the grid, where the values are not used) into the
+// ring slot st.cur, by lane 0.  The slot's previous column was last read at
+// the previous position: the warp's reads are ordered before the copy by the
+// warp barrier and the proxy fence.
+template <typename T, int K, int S>
+__device__ __forceinline__ void ring_issue(T *ring, unsigned long long *bars, RingState &st,
+                                           const T *__restrict__ half, const T *__restrict__ node, int p,
+                                           int Nr, int lane)
+{
+    constexpr int NP = 32 * K;
+    constexpr unsigned HB = kNCH * NP * sizeof(T), NB = kNCN * NP * sizeof(T);
+    const int s = st.cur;
+    __syncwarp();
+    if (lane == 0) {
+        int c = p - 1;
+        c = c < 0 ? 0 : (c > Nr - 1 ? Nr - 1 : c);
+        T *slot = ring + (size_t)s * kSlotCols * NP;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect(bars + s, HB + NB);
+        bulk_fetch(slot, half + (size_t)c * kNCH * NP, HB, bars + s);
+        bulk_fetch(slot + kSlotNode * NP, node + (size_t)c * kNCN * NP, NB, bars + s);
+    }
+    st.issue_ph ^= 1u << s;
+    st.cur = s == S - 1 ? 0 : s + 1;
+}
+
+// Wait for the copy into slot s (the oldest one not yet waited for).
+template <int S>
+__device__ __forceinline__ void ring_wait(unsigned long long *bars, RingState &st, int s, int *err)
+{
+    if (!mbar_wait(bars + s, (st.wait_ph >> s) & 1u)) atomicExch(err, 1);
+    st.wait_ph ^= 1u << s;
 }
 
 // The four-step sweep copies the Phi values of up to kObsCols observer
@@ -595,7 +696,8 @@ constexpr size_t multi_obs_scratch_elems_per_warp()
 }
 
 template <typename T, int K, int LV>
-__device__ __forceinline__ void multi_body(T *ring, int i0, int i1, int lane, const T *__restrict__ u_in,
+__device__ __forceinline__ void multi_body(T *ring, unsigned long long *bars, RingState &rs, int *err, int i0,
+                                           int i1, int lane, const T *__restrict__ u_in,
                                            T *__restrict__ u_out, const T *__restrict__ half,
                                            const T *__restrict__ node, int Nr, T en, int mask,
                                            const int (&oc)[kObsCols], T *__restrict__ scr)
@@ -612,18 +714,15 @@ __device__ __forceinline__ void multi_body(T *ring, int i0, int i1, int lane, co
         zero_col<T, K>(um[l]);
     }
     const int pa = i0 - LV, pb = i1 + LV - 1;
-    ring_fetch<T, K>(ring, half, node, pa, Nr, row);
+    ring_issue<T, K, S>(ring, bars, rs, half, node, pa, Nr, lane);
     T cn[4][K];
     if (pa >= 0) load_state<T, K, true>(u_in + (size_t)pa * SP + row, cn);
     else zero_col<T, K>(cn);
-    int cur = 0;
+    int cur = rs.cur == 0 ? S - 1 : rs.cur - 1;   // the slot of position pa
     for (int p = pa; p <= pb; ++p) {
         const int nxt = cur == S - 1 ? 0 : cur + 1;
-        if (p + 1 <= pb)
-            ring_fetch<T, K>(ring + nxt * kSlotCols * NP, half, node, p + 1, Nr, row);
-        else
-            cp_async_commit();
-        cp_async_wait_one();
+        if (p + 1 <= pb) ring_issue<T, K, S>(ring, bars, rs, half, node, p + 1, Nr, lane);
+        ring_wait<S>(bars, rs, cur, err);
         T cu[4][K];   // level l - 1 at column p - l + 1
 #pragma unroll
         for (int c = 0; c < 4; ++c)
@@ -676,12 +775,12 @@ __device__ __forceinline__ void multi_body(T *ring, int i0, int i1, int lane, co
                         }
         cur = nxt;
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // The sweep, with the waveform samples formed after its loop (see kObsCols).
 template <typename T, int K, int W, int LV>
-__device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, const T *__restrict__ u_in,
+__device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, RingState &rs, int *err,
+                                            const T *__restrict__ u_in,
                                             T *__restrict__ u_out, const T *__restrict__ half,
                                             const T *__restrict__ node, int Nr, T en,
                                             const WaveArgs &wa, int mask, const int (&off)[LV],
@@ -691,6 +790,8 @@ __device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, const T *__re
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     T *ring = reinterpret_cast<T *>(sh_raw) + (size_t)wib * (LV + 1) * kSlotCols * NP;
+    unsigned long long *bars =
+        reinterpret_cast<unsigned long long *>(sh_raw + multi_ring_bytes<T, K, W, LV>()) + wib * (LV + 1);
     int i0, i1, left;
     warp_range<W>(Nr, wib, &i0, &i1, &left);
     if (i1 <= i0) return;
@@ -717,7 +818,7 @@ __device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, const T *__re
             }
     constexpr size_t kWarpScr = (size_t)kObsCols * LV * 2 * NP;   // per warp
     T *wscr = scr + (size_t)(blockIdx.x * W + wib) * kWarpScr;
-    multi_body<T, K, LV>(ring, i0, i1, lane, u_in, u_out, half, node, Nr, en, mask, oc, wscr);
+    multi_body<T, K, LV>(ring, bars, rs, err, i0, i1, lane, u_in, u_out, half, node, Nr, en, mask, oc, wscr);
     if (n == 0) return;
     const int row = lane * K;
 #pragma unroll
@@ -747,6 +848,16 @@ lw_multi_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__
                            int *err, T *scr)
 {
     extern __shared__ __align__(16) unsigned char sh_raw[];
+    constexpr int S = LV + 1;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned long long *bars =
+        reinterpret_cast<unsigned long long *>(sh_raw + multi_ring_bytes<T, K, W, LV>()) + wib * S;
+    if (lane == 0) {
+        for (int q = 0; q < S; ++q) mbar_init(bars + q);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    RingState rs{0, 0u, 0u};
     for (int g = 0; g < n_groups; ++g) {
         const T *in = (g & 1) ? u1 : u0;
         T *out = (g & 1) ? u0 : u1;
@@ -758,9 +869,14 @@ lw_multi_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__
             if (wa.write && (t + l + 1) % k == 0) mask |= 1 << l;
             off[l] = (t + l + 1) / k - 1;
         }
-        multi_sweep<T, K, W, LV>(sh_raw, in, out, half, node, Nr, en, wa, mask, off, scr);
+        multi_sweep<T, K, W, LV>(sh_raw, rs, err, in, out, half, node, Nr, en, wa, mask, off, scr);
         if (g + 1 < n_groups && !neighbour_barrier(flags, (unsigned)(g + 1), err)) break;
     }
+    // every copy issued has been waited for, unless a wait gave up: then wait
+    // (bounded) for the last copy into each slot before the block exits
+    if (rs.wait_ph != rs.issue_ph && lane == 0)
+        for (int q = 0; q < S; ++q)
+            if (((rs.wait_ph ^ rs.issue_ph) >> q) & 1u) mbar_wait(bars + q, ((rs.issue_ph >> q) & 1u) ^ 1u);
     if (wa.write) advance_sample(wa, (LV * n_groups) / k);
 }
 
