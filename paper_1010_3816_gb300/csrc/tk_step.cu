@@ -719,6 +719,15 @@ __device__ __forceinline__ void multi_body(T *ring, unsigned long long *bars, Ri
     if (pa >= 0) load_state<T, K, true>(u_in + (size_t)pa * SP + row, cn);
     else zero_col<T, K>(cn);
     int cur = rs.cur == 0 ? S - 1 : rs.cur - 1;   // the slot of position pa
+    // the warp's observer columns span [olo, ohi] (olo > ohi: none)
+    int olo = 0x7fffffff, ohi = -1;
+#pragma unroll
+    for (int h = 0; h < kObsCols; ++h)
+        if (oc[h] >= 0) {
+            olo = oc[h] < olo ? oc[h] : olo;
+            ohi = oc[h] > ohi ? oc[h] : ohi;
+        }
+    if (!mask) ohi = -1;
     for (int p = pa; p <= pb; ++p) {
         const int nxt = cur == S - 1 ? 0 : cur + 1;
         if (p + 1 <= pb) ring_issue<T, K, S>(ring, bars, rs, half, node, p + 1, Nr, lane);
@@ -728,14 +737,16 @@ __device__ __forceinline__ void multi_body(T *ring, unsigned long long *bars, Ri
         for (int c = 0; c < 4; ++c)
 #pragma unroll
             for (int t = 0; t < K; ++t) cu[c][t] = cn[c][t];
-        if (p + 1 <= pb && p + 1 < Nr)
+        if (p + 1 <= pb && p + 1 >= 0 && p + 1 < Nr)
             load_state<T, K, true>(u_in + (size_t)(p + 1) * SP + row, cn);
         else
             zero_col<T, K>(cn);
-        // the levels without branches: every node and half node is formed
-        // (a ring slot is in range for any column) and the values outside a
-        // level's columns are then replaced by zero; the stores follow
-        T lv[LV][2][K];   // Phi at each level, for the waveform copies
+        // Every node and half node is formed, also outside a level's valid
+        // columns [i0 - (LV - l), i1 + LV - l): the values there are finite
+        // (formed from finite tables of a column clamped into the grid, and
+        // from zeros beyond its edges) and feed only other values outside, so
+        // they need no masking.  The node values on the radial edges c = 0
+        // and c = Nr - 1 are set to zero (Sec. 3.2), at every level.
 #pragma unroll
         for (int l = 1; l <= LV; ++l) {
             const int c = p - l;
@@ -745,34 +756,27 @@ __device__ __forceinline__ void multi_body(T *ring, unsigned long long *bars, Ri
             T hp[4][K], uc[4][K];
             half_node<T, K>(um[l - 1], cu, tab + row, hp);
             full_node<T, K>(hm[l - 1], hp, um[l - 1], tab + kSlotNode * NP + row, en, uc);
-            const bool hv = c >= i0 - (LV - l) - 1 && c >= 0 && c + 1 < Nr;
-            const bool nv = c >= i0 - (LV - l) && c >= 1 && c <= Nr - 2;   // implies hv
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
                 for (int t = 0; t < K; ++t) {
                     um[l - 1][q][t] = cu[q][t];
-                    hm[l - 1][q][t] = hv ? hp[q][t] : T(0);
-                    cu[q][t] = nv ? uc[q][t] : T(0);
+                    hm[l - 1][q][t] = hp[q][t];
+                    cu[q][t] = uc[q][t];
                 }
+            if (c == 0 || c == Nr - 1) zero_col<T, K>(cu);
+            // the Phi values of an observer column at a level where an outer
+            // step ends, for the samples formed after the loop
+            if (c >= olo && c <= ohi && ((mask >> (l - 1)) & 1))
 #pragma unroll
-            for (int t = 0; t < K; ++t) {
-                lv[l - 1][0][t] = cu[0][t];
-                lv[l - 1][1][t] = cu[1][t];
-            }
+                for (int h = 0; h < kObsCols; ++h)
+                    if (c == oc[h]) {
+                        T *d = scr + ((size_t)h * LV + (l - 1)) * 2 * NP + row;
+                        stk<T, K>(d, cu[0]);
+                        stk<T, K>(d + NP, cu[1]);
+                    }
         }
         if (p - LV >= i0) store_col<T, K>(u_out + (size_t)(p - LV) * SP + row, cu);
-        if (mask)
-#pragma unroll
-            for (int l = 1; l <= LV; ++l)
-                if ((mask >> (l - 1)) & 1)
-#pragma unroll
-                    for (int h = 0; h < kObsCols; ++h)
-                        if (p - l == oc[h]) {
-                            T *d = scr + ((size_t)h * LV + (l - 1)) * 2 * NP + row;
-                            stk<T, K>(d, lv[l - 1][0]);
-                            stk<T, K>(d + NP, lv[l - 1][1]);
-                        }
         cur = nxt;
     }
 }
