@@ -308,11 +308,14 @@ tk_status tk_batch_create(tk_batch **out, tk_solver *const *members, int n);
 /* Advance every member by n outer steps (samples appended as by tk_step). */
 tk_status tk_batch_step(tk_batch *B, int n);
 
-/* Autotuner: time trial_steps outer steps for each candidate segment length
- * (columns per work item: 4 .. 128) on the batch's own data, restore every
- * member's state and sample counter after each trial, and keep the fastest.
- * Writes the chosen length and its time per outer step (ms).  Needs device
- * memory for one copy of every member's state. */
+/* Autotuner (the counterpart of the paper's tuning of the work-group size,
+ * Sec. 4): time trial_steps outer steps for every pair of a segment length
+ * (columns per work item: 4 .. 128) and a grid size (1 .. the resident
+ * maximum of blocks per SM) on the batch's own data, restore every member's
+ * state and sample counter after each trial, and keep the fastest pair.
+ * Writes the chosen length and its time per outer step (ms); the chosen grid
+ * is reported by tk_batch_info.  Needs device memory for one copy of every
+ * member's state. */
 tk_status tk_batch_tune(tk_batch *B, int trial_steps, int *best_seg, double *best_ms_per_step);
 
 /* Set the segment length directly (>= 2). */

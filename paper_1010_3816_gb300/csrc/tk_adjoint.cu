@@ -786,7 +786,8 @@ extern "C" tk_status tk_param_gradient(tk_solver *S, int param, const double *dL
             e = tk::launch_invert_tortoise(P, S->rs_min, S->drs, S->Nr, tx, tx + S->Nr, S->stream);
             if (e == cudaSuccess)
                 e = tk::launch_coeff_tables(P, S->variable, S->Nr, S->Nth, S->NP, S->drs, dt_in, tx,
-                                            tx + S->Nr, tang, 0, thalf, tnode, tb, tw, S->stream);
+                                            tx + S->Nr, tang, 0, thalf, tnode, tb, tw, nullptr,
+                                            nullptr, S->stream);
             if (e == cudaSuccess) e = tk::launch_axpy(nh, wgt[q], thalf, S->dhalf, S->stream);
             if (e == cudaSuccess) e = tk::launch_axpy(nn, wgt[q], tnode, S->dnode, S->stream);
             if (e == cudaSuccess) e = tk::launch_axpy(nb, wgt[q], tb, S->db_node, S->stream);

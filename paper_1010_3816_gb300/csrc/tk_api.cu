@@ -47,7 +47,7 @@ void release(tk_solver *S)
     void *ptrs[] = {S->u[0], S->u[1], S->half, S->node, S->b_node, S->w_row,
                     S->x_node, S->x_half, S->ang, S->staging, S->flag, S->stiff, S->ctr, S->wave,
                     S->adj[0], S->adj[1], S->u_init, S->dhalf, S->dnode, S->db_node, S->pflags,
-                    S->obs_scr, S->xbuf};
+                    S->obs_scr, S->xbuf, S->cmp, S->gpm};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (int k = 0; k < 2; ++k)
@@ -129,6 +129,8 @@ void fill_launch(const tk_solver *S, tk::StepLaunch &L)
     L.dt_inner = S->dt / S->substeps;
     L.half = S->half;
     L.node = S->node;
+    L.cmp = S->cmp;
+    L.gpm = S->gpm;
     L.wave_cap = S->wave_cap;
     L.wave = S->wave;
     L.w_row = S->w_row;
@@ -242,6 +244,10 @@ tk_status tk_make_grid(tk_solver **out, double rstar_min, double rstar_max, int 
     if (st == TK_OK) st = alloc(S, &S->u[1], se * S->esz);
     if (st == TK_OK) st = alloc(S, &S->half, (size_t)Nr * tk::kNCH * S->NP * S->esz);
     if (st == TK_OK) st = alloc(S, &S->node, (size_t)Nr * tk::kNCN * S->NP * S->esz);
+    if (st == TK_OK && precision == TK_PREC_F32)
+        st = alloc(S, (void **)&S->cmp, (size_t)Nr * tk::kNCC * S->NP * sizeof(float));
+    if (st == TK_OK && precision == TK_PREC_F32)
+        st = alloc(S, (void **)&S->gpm, (size_t)2 * S->NP * sizeof(float));
     if (st == TK_OK) st = alloc(S, (void **)&S->b_node, (size_t)Nr * S->NP * sizeof(double));
     if (st == TK_OK) st = alloc(S, (void **)&S->w_row, (size_t)S->NP * sizeof(double));
     if (st == TK_OK) st = alloc(S, (void **)&S->x_node, (size_t)Nr * sizeof(double));
@@ -287,7 +293,7 @@ tk_status tk_precompute_coeffs(tk_solver *S, double a, double M, int s, int m)
     TK_CUDA(S, tk::launch_coeff_tables(S->kerr, S->variable, S->Nr, S->Nth, S->NP, S->drs,
                                        S->dt / S->substeps, S->x_node, S->x_half, S->ang,
                                        S->precision, S->half, S->node, S->b_node, S->w_row,
-                                       S->stream));
+                                       S->cmp, S->gpm, S->stream));
     S->have_coeffs = true;
     S->have_state = false;
     S->epoch++;   // the tables' time step may have changed: recapture graphs
@@ -306,7 +312,7 @@ tk_status tk_precompute_coeffs(tk_solver *S, double a, double M, int s, int m)
             TK_CUDA(S, tk::launch_coeff_tables(S->kerr, S->variable, S->Nr, S->Nth, S->NP, S->drs,
                                                S->dt / S->substeps, S->x_node, S->x_half, S->ang,
                                                S->precision, S->half, S->node, S->b_node,
-                                               S->w_row, S->stream));
+                                               S->w_row, S->cmp, S->gpm, S->stream));
         }
     }
     return TK_OK;

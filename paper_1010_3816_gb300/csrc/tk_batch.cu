@@ -481,13 +481,19 @@ tk_status tk_batch_tune(tk_batch *B, int trial_steps, int *best_seg, double *bes
     TKB_CUDA(B, cudaStreamSynchronize(B->stream));
     const int old_chunk = B->graph_chunk;
     B->graph_chunk = 0;   // trials launch directly
+    // the search space: segment length (columns per work item) x grid size
+    // (blocks per SM, up to the resident maximum; fewer blocks leave each
+    // warp more items of the queue)
     const int candidates[] = {4, 8, 12, 16, 24, 32, 48, 64, 96, 128};
-    int best = B->seg;
+    const int sms = B->mem[0]->num_sms, max_per_sm = tk::batch_resident_blocks(B->precision);
+    int best = B->seg, best_blocks = B->blocks;
     double best_t = 1e300;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    for (int per_sm = max_per_sm; per_sm >= 1 && st == TK_OK; --per_sm)
     for (int seg : candidates) {
+        B->blocks = sms * per_sm;
         st = build_items(B, seg);
         if (st != TK_OK) break;
         st = upload_members(B);
@@ -502,6 +508,7 @@ tk_status tk_batch_tune(tk_batch *B, int trial_steps, int *best_seg, double *bes
         if (ms < best_t) {
             best_t = ms;
             best = seg;
+            best_blocks = B->blocks;
         }
         for (int k = 0; k < B->n; ++k) {   // undo the trial
             tk_solver *S = B->mem[k];
@@ -515,6 +522,7 @@ tk_status tk_batch_tune(tk_batch *B, int trial_steps, int *best_seg, double *bes
     cudaEventDestroy(e1);
     for (void *p : keep) cudaFree(p);
     B->graph_chunk = old_chunk;
+    B->blocks = best_blocks;
     if (st != TK_OK) return st;
     st = build_items(B, best);
     if (st != TK_OK) return st;

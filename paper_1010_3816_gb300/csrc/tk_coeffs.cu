@@ -197,7 +197,8 @@ __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int 
                                     const double *__restrict__ x_half,
                                     const double *__restrict__ ang, T *__restrict__ half,
                                     T *__restrict__ node, double *__restrict__ b_node,
-                                    double *__restrict__ w_row)
+                                    double *__restrict__ w_row, float *__restrict__ cmp,
+                                    float *__restrict__ gpm, F32Derive fd)
 {
     const int jp = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
@@ -209,6 +210,8 @@ __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int 
     for (int q = 0; q < kNCH; ++q) hv[q] = 0.0;
     for (int q = 0; q < kNCN; ++q) nv[q] = 0.0;
     double bn = 0.0;
+    double c4n = 0.0, c4h = 0.0;   // c4 at the node and at the half node
+    double gpv = 0.0, gmv = 0.0;   // theta-only stencil factors of the row
     const double dth = M_PI / Nth;
     const double ith2 = 1.0 / (dth * dth), i2th = 1.0 / (2.0 * dth);
     const double p = (variable == 0 && (abs(P.m) & 1)) ? -1.0 : 1.0;   // ghost parity
@@ -220,10 +223,20 @@ __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int 
         //   regularised: A+- = c4 ang[.]  (self-adjoint form, no ghosts)
         const double Ap = (variable != 0) ? ang[jp] : 0.0;
         const double Am = (variable != 0) ? ang[NP + jp] : 0.0;
+        if (variable != 0) {
+            gpv = Ap;
+            gmv = Am;
+        } else {
+            double sn, cs;
+            sincos(th, &sn, &cs);
+            gpv = (jp == Nth - 1) ? 0.0 : ith2 + (cs / sn) * i2th;   // ghosts folded on the edge rows
+            gmv = (jp == 0) ? 0.0 : ith2 - (cs / sn) * i2th;
+        }
         {   // node r*_i, Eq. (lw2), step dt
             const Raw c = raw_coefficients(P, variable, x_node[i], th);
             bn = c.b;
             if (i > 0 && i < Nr - 1) {
+                c4n = c.c4;
                 const double h2 = 0.5 * dt;
                 const double B = dt * c.b / drs;
                 const double g1r = dt * c.c1r / drs, g1i = dt * c.c1i / drs;
@@ -256,6 +269,7 @@ __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int 
         }
         if (i < Nr - 1) {   // half node r*_{i+1/2}, Eq. (lw1), step dt/2
             const Raw c = raw_coefficients(P, variable, x_half[i], th);
+            c4h = c.c4;
             const double dtau = 0.5 * dt, e2 = 0.5 * dtau;
             const double B = dtau * c.b / drs;
             const double g1r = dtau * c.c1r / drs, g1i = dtau * c.c1i / drs;
@@ -288,8 +302,63 @@ __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int 
     } else if (i == 0 && w_row) {
         w_row[jp] = 0.0;
     }
-    for (int q = 0; q < kNCH; ++q) hcol[(size_t)q * NP] = (T)hv[q];
-    for (int q = 0; q < kNCN; ++q) ncol[(size_t)q * NP] = (T)nv[q];
+    if constexpr (sizeof(T) == 4) {
+        // FP32: sixteen entries rounded from FP64, the other five derived from
+        // them in FP32 exactly as the compact-table kernel derives them
+        float cv[kNCC];
+        cv[C_HP] = (float)hv[H_HP];
+        cv[C_PAR] = (float)hv[H_PAR];
+        cv[C_PI] = (float)hv[H_PI];
+        cv[C_FAR] = (float)hv[H_FAR];
+        cv[C_FAI] = (float)hv[H_FAI];
+        cv[C_FCR] = (float)hv[H_FCR];
+        cv[C_FCI] = (float)hv[H_FCI];
+        cv[C_C4H] = (jp < Nth && i < Nr - 1) ? (float)(0.25 * dt * c4h) : 0.0f;
+        cv[C_B] = (float)nv[N_B];
+        cv[C_PMR] = (float)nv[N_PMR];
+        cv[C_C2I] = (float)nv[N_C2I];
+        cv[C_FPR] = (float)nv[N_FPR];
+        cv[C_FPI] = (float)nv[N_FPI];
+        cv[C_FMR] = (float)nv[N_FMR];
+        cv[C_FMI] = (float)nv[N_FMI];
+        cv[C_C4N] = (jp < Nth && i > 0 && i < Nr - 1) ? (float)(0.25 * dt * 0.5 * dt * c4n) : 0.0f;
+        const float gp = (float)gpv, gm = (float)gmv;
+        if (i == 0 && gpm) {
+            gpm[jp] = gp;
+            gpm[NP + jp] = gm;
+        }
+        float h32[kNCH], n32[kNCN];
+        h32[H_HP] = cv[C_HP];
+        h32[H_HQ] = __fadd_rn(fd.ih, -cv[C_HP]);
+        h32[H_PAR] = cv[C_PAR];
+        h32[H_PCR] = __fadd_rn(cv[C_PAR], __fmaf_rn(fd.t2, cv[C_HP], -1.0f));
+        h32[H_PI] = cv[C_PI];
+        h32[H_FAR] = cv[C_FAR];
+        h32[H_FAI] = cv[C_FAI];
+        h32[H_FCR] = cv[C_FCR];
+        h32[H_FCI] = cv[C_FCI];
+        h32[H_KP] = __fmul_rn(cv[C_C4H], gp);
+        h32[H_KM] = __fmul_rn(cv[C_C4H], gm);
+        n32[N_B] = cv[C_B];
+        n32[N_PPR] = __fmaf_rn(fd.bn2, cv[C_B], cv[C_PMR]);
+        n32[N_PMR] = cv[C_PMR];
+        n32[N_C2I] = cv[C_C2I];
+        n32[N_FPR] = cv[C_FPR];
+        n32[N_FPI] = cv[C_FPI];
+        n32[N_FMR] = cv[C_FMR];
+        n32[N_FMI] = cv[C_FMI];
+        n32[N_KP] = __fmul_rn(cv[C_C4N], gp);
+        n32[N_KM] = __fmul_rn(cv[C_C4N], gm);
+        for (int q = 0; q < kNCH; ++q) hcol[(size_t)q * NP] = h32[q];
+        for (int q = 0; q < kNCN; ++q) ncol[(size_t)q * NP] = n32[q];
+        if (cmp) {
+            float *ccol = cmp + (size_t)i * kNCC * NP + jp;
+            for (int q = 0; q < kNCC; ++q) ccol[(size_t)q * NP] = cv[q];
+        }
+    } else {
+        for (int q = 0; q < kNCH; ++q) hcol[(size_t)q * NP] = (T)hv[q];
+        for (int q = 0; q < kNCN; ++q) ncol[(size_t)q * NP] = (T)nv[q];
+    }
     b_node[(size_t)i * NP + jp] = bn;
 }
 
@@ -349,8 +418,10 @@ cudaError_t launch_invert_tortoise(const Kerr &P, double rs_min, double drs, int
 cudaError_t launch_coeff_tables(const Kerr &P, int variable, int Nr, int Ntheta, int NP,
                                 double drs, double dt_inner, const double *x_node,
                                 const double *x_half, double *ang, int precision, void *half,
-                                void *node, double *b_node, double *w_row, cudaStream_t st)
+                                void *node, double *b_node, double *w_row, float *cmp, float *gpm,
+                                cudaStream_t st)
 {
+    const F32Derive fd = f32_derive(dt_inner);
     if (variable != 0) {
         regular_stencil_kernel<<<NP, 32, 0, st>>>(P.s, P.m, Ntheta, NP, ang);
         cudaError_t e = cudaGetLastError();
@@ -361,11 +432,12 @@ cudaError_t launch_coeff_tables(const Kerr &P, int variable, int Nr, int Ntheta,
     if (precision == 0)
         coeff_tables_kernel<double><<<grid, block, 0, st>>>(P, variable, Nr, Ntheta, NP, drs, dt_inner,
                                                              x_node, x_half, ang, (double *)half,
-                                                             (double *)node, b_node, w_row);
+                                                             (double *)node, b_node, w_row, nullptr,
+                                                             nullptr, fd);
     else
         coeff_tables_kernel<float><<<grid, block, 0, st>>>(P, variable, Nr, Ntheta, NP, drs, dt_inner,
                                                             x_node, x_half, ang, (float *)half,
-                                                            (float *)node, b_node, w_row);
+                                                            (float *)node, b_node, w_row, cmp, gpm, fd);
     return cudaGetLastError();
 }
 

@@ -45,6 +45,33 @@ enum { H_HP = 0, H_HQ, H_PAR, H_PCR, H_PI, H_FAR, H_FAI, H_FCR, H_FCI, H_KP, H_K
 // the poles (KM = 0 on row 0, KP = 0 on row Ntheta-1).  Padding rows are all 0.
 enum { N_B = 0, N_PPR, N_PMR, N_C2I, N_FPR, N_FPI, N_FMR, N_FMI, N_KP, N_KM };
 
+// FP32 tables.  Five of the 21 entries follow from the others and from
+// theta-only factors: HQ = 1/e2 - HP, PCR = PAR + (2 e2 HP - 1) (both from
+// HP e2 = 1/2 + B at the half node), PPR = PMR + (2/eh) B_tab (B_tab = eh B at
+// the node), and KP, KM = C4 gp_j, C4 gm_j with C4 the 2-D factor (e2 c4 at
+// the half node, eh dt/2 c4 at the node) and gp, gm the theta-only stencil
+// factors of row j (regularised: the self-adjoint stencil's face weights;
+// literal: 1/dth^2 +- cot(theta_j)/(2 dth); zero where a ghost was folded).
+// The FP32 tables hold those five entries as exactly these FP32 operations on
+// the FP32 values of the others (F32Derive), so that a kernel may read all 21
+// or read the 16 of the compact copy cmp[i][kNCC][jp] (the four-step sweep:
+// 24 % fewer table bytes) and derive the rest with the same operations,
+// bit-identically.
+constexpr int kNCC = 16;
+enum { C_HP = 0, C_PAR, C_PI, C_FAR, C_FAI, C_FCR, C_FCI, C_C4H,
+       C_B, C_PMR, C_C2I, C_FPR, C_FPI, C_FMR, C_FMI, C_C4N };
+struct F32Derive {
+    float ih;    // 1 / e2 (e2 = eh = dt/4)
+    float t2;    // 2 e2
+    float bn2;   // 2 / eh
+};
+// The FP32 constants of the derivation for an inner step dt.
+inline F32Derive f32_derive(double dt_inner)
+{
+    const double e2 = 0.25 * dt_inner;
+    return F32Derive{(float)(1.0 / e2), (float)(2.0 * e2), (float)(2.0 / e2)};
+}
+
 struct Kerr {
     double M, a;  // black-hole mass and spin
     int s, m;     // spin weight, azimuthal mode
@@ -78,10 +105,13 @@ struct WaveRead {
 // ---- coefficient precompute (tk_coeffs.cu) ----
 cudaError_t launch_invert_tortoise(const Kerr &P, double rs_min, double drs, int Nr,
                                    double *x_node, double *x_half, cudaStream_t st);
+// FP32 (precision 1) also writes the compact tables cmp and the theta
+// factors gpm[2][NP] (gp, then gm); both may be NULL for FP64.
 cudaError_t launch_coeff_tables(const Kerr &P, int variable, int Nr, int Ntheta, int NP,
                                 double drs, double dt_inner, const double *x_node,
                                 const double *x_half, double *ang, int precision, void *half,
-                                void *node, double *b_node, double *w_row, cudaStream_t st);
+                                void *node, double *b_node, double *w_row, float *cmp, float *gpm,
+                                cudaStream_t st);
 
 cudaError_t launch_stiffness(const Kerr &P, int variable, int Nr, int Ntheta, int NP,
                              const double *x_node, const double *ang, unsigned long long *out,
@@ -117,6 +147,8 @@ struct StepLaunch {
     void *u_out;
     const void *half;
     const void *node;
+    const float *cmp;     // FP32: compact tables [i][kNCC][jp] (the four-step sweep)
+    const float *gpm;     // FP32: theta factors gp[NP], gm[NP]
     // waveform (only on the last inner step of an outer step)
     int write_wave;
     const long long *sample_ctr;  // device: index of the sample the outer step writes

@@ -19,6 +19,7 @@ struct tk_solver {
     void *u[2] = {nullptr, nullptr};
     int cur = 0;
     void *half = nullptr, *node = nullptr;
+    float *cmp = nullptr, *gpm = nullptr;   // FP32: compact tables, theta factors (tk_internal.h)
     double *b_node = nullptr, *w_row = nullptr, *x_node = nullptr, *x_half = nullptr;
     double *ang = nullptr;      // regularised angular stencil [2][NP]
     double *staging = nullptr;  // 4 * Nth * Nr doubles, for host transfers

@@ -202,10 +202,9 @@ __device__ __forceinline__ void st2(float *v, int t, float2 x)
 // PI_TERM = false leaves that term out (the derivative of the step with
 // respect to the tables, where it is constant).
 template <typename T, int K, bool PI_TERM = true>
-__device__ __forceinline__ void half_node(const T (&a)[4][K], const T (&c)[4][K],
-                                          const T *__restrict__ tab, T (&h)[4][K])
+__device__ __forceinline__ void half_node_q(const T (&a)[4][K], const T (&c)[4][K],
+                                            const T (&q)[kNCH][K], T (&h)[4][K])
 {
-    constexpr int NP = 32 * K;
     const FmaK<T> k1 = fma_k<T>();
     T sR[K], sI[K], upR[K], upI[K], dnR[K], dnI[K];
     if constexpr (sizeof(T) == 4 && K % 2 == 0) {
@@ -223,9 +222,6 @@ __device__ __forceinline__ void half_node(const T (&a)[4][K], const T (&c)[4][K]
     }
     theta_neighbours<T, K>(sR, upR, dnR);
     theta_neighbours<T, K>(sI, upI, dnI);
-    T q[kNCH][K];
-#pragma unroll
-    for (int k = 0; k < kNCH; ++k) ldk<T, K>(tab + k * NP, q[k]);
     if constexpr (sizeof(T) == 4 && K % 2 == 0) {
 #pragma unroll
         for (int t = 0; t < K; t += 2) {
@@ -303,11 +299,10 @@ __device__ __forceinline__ void half_node(const T (&a)[4][K], const T (&c)[4][K]
 
 // Eq. (lw2): u^{n+1}_i from hm = u^{n+1/2}_{i-1/2}, hp = u^{n+1/2}_{i+1/2}, u = u^n_i.
 template <typename T, int K>
-__device__ __forceinline__ void full_node(const T (&hm)[4][K], const T (&hp)[4][K],
-                                          const T (&u)[4][K], const T *__restrict__ tab,
-                                          const T e, T (&o)[4][K])
+__device__ __forceinline__ void full_node_q(const T (&hm)[4][K], const T (&hp)[4][K],
+                                            const T (&u)[4][K], const T (&q)[kNCN][K],
+                                            const T e, T (&o)[4][K])
 {
-    constexpr int NP = 32 * K;
     const FmaK<T> k1 = fma_k<T>();
     T sR[K], sI[K], upR[K], upI[K], dnR[K], dnI[K];
     if constexpr (sizeof(T) == 4 && K % 2 == 0) {
@@ -325,9 +320,6 @@ __device__ __forceinline__ void full_node(const T (&hm)[4][K], const T (&hp)[4][
     }
     theta_neighbours<T, K>(sR, upR, dnR);
     theta_neighbours<T, K>(sI, upI, dnI);
-    T q[kNCN][K];
-#pragma unroll
-    for (int k = 0; k < kNCN; ++k) ldk<T, K>(tab + k * NP, q[k]);
     if constexpr (sizeof(T) == 4 && K % 2 == 0) {
         const float2 e2 = make_float2(e, e);
 #pragma unroll
@@ -391,6 +383,106 @@ __device__ __forceinline__ void full_node(const T (&hm)[4][K], const T (&hp)[4][
         y = fma(q[N_KP][t], upI[t], y);
         y = fma(q[N_KM][t], dnI[t], y);
         o[3][t] = y;
+    }
+}
+
+// The node routines with their tables read from a table column (the 21-entry
+// layout of both precisions).
+template <typename T, int K, bool PI_TERM = true>
+__device__ __forceinline__ void half_node(const T (&a)[4][K], const T (&c)[4][K],
+                                          const T *__restrict__ tab, T (&h)[4][K])
+{
+    constexpr int NP = 32 * K;
+    T q[kNCH][K];
+#pragma unroll
+    for (int k = 0; k < kNCH; ++k) ldk<T, K>(tab + k * NP, q[k]);
+    half_node_q<T, K, PI_TERM>(a, c, q, h);
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void full_node(const T (&hm)[4][K], const T (&hp)[4][K],
+                                          const T (&u)[4][K], const T *__restrict__ tab,
+                                          const T e, T (&o)[4][K])
+{
+    constexpr int NP = 32 * K;
+    T q[kNCN][K];
+#pragma unroll
+    for (int k = 0; k < kNCN; ++k) ldk<T, K>(tab + k * NP, q[k]);
+    full_node_q<T, K>(hm, hp, u, q, e, o);
+}
+
+// FP32 compact tables (kNCC entries per column): the 21 entries of a column
+// from its 16 stored ones, the lane's theta factors gp, gm and the constants
+// of F32Derive, by the FP32 operations with which the table builder formed
+// the full tables (so both layouts give the same bits).
+template <int K>
+__device__ __forceinline__ void derive_half(const float *__restrict__ tab, const float (&gp)[K],
+                                            const float (&gm)[K], const F32Derive &fd,
+                                            float (&q)[kNCH][K])
+{
+    constexpr int NP = 32 * K;
+    float C4[K];
+    ldk<float, K>(tab + C_HP * NP, q[H_HP]);
+    ldk<float, K>(tab + C_PAR * NP, q[H_PAR]);
+    ldk<float, K>(tab + C_PI * NP, q[H_PI]);
+    ldk<float, K>(tab + C_FAR * NP, q[H_FAR]);
+    ldk<float, K>(tab + C_FAI * NP, q[H_FAI]);
+    ldk<float, K>(tab + C_FCR * NP, q[H_FCR]);
+    ldk<float, K>(tab + C_FCI * NP, q[H_FCI]);
+    ldk<float, K>(tab + C_C4H * NP, C4);
+    if constexpr (K % 2 == 0) {
+        const float2 ih = make_float2(fd.ih, fd.ih), t2 = make_float2(fd.t2, fd.t2);
+        const float2 m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+        for (int t = 0; t < K; t += 2) {
+            const float2 HP = pr2(q[H_HP], t), C = pr2(C4, t);
+            st2(q[H_HQ], t, __fadd2_rn(ih, ng2(HP)));
+            st2(q[H_PCR], t, __fadd2_rn(pr2(q[H_PAR], t), __ffma2_rn(t2, HP, m1)));
+            st2(q[H_KP], t, __fmul2_rn(C, pr2(gp, t)));
+            st2(q[H_KM], t, __fmul2_rn(C, pr2(gm, t)));
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            q[H_HQ][t] = __fadd_rn(fd.ih, -q[H_HP][t]);
+            q[H_PCR][t] = __fadd_rn(q[H_PAR][t], __fmaf_rn(fd.t2, q[H_HP][t], -1.0f));
+            q[H_KP][t] = __fmul_rn(C4[t], gp[t]);
+            q[H_KM][t] = __fmul_rn(C4[t], gm[t]);
+        }
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void derive_node(const float *__restrict__ tab, const float (&gp)[K],
+                                            const float (&gm)[K], const F32Derive &fd,
+                                            float (&q)[kNCN][K])
+{
+    constexpr int NP = 32 * K;
+    float C4[K];
+    ldk<float, K>(tab + (C_B - C_B) * NP, q[N_B]);
+    ldk<float, K>(tab + (C_PMR - C_B) * NP, q[N_PMR]);
+    ldk<float, K>(tab + (C_C2I - C_B) * NP, q[N_C2I]);
+    ldk<float, K>(tab + (C_FPR - C_B) * NP, q[N_FPR]);
+    ldk<float, K>(tab + (C_FPI - C_B) * NP, q[N_FPI]);
+    ldk<float, K>(tab + (C_FMR - C_B) * NP, q[N_FMR]);
+    ldk<float, K>(tab + (C_FMI - C_B) * NP, q[N_FMI]);
+    ldk<float, K>(tab + (C_C4N - C_B) * NP, C4);
+    if constexpr (K % 2 == 0) {
+        const float2 bn2 = make_float2(fd.bn2, fd.bn2);
+#pragma unroll
+        for (int t = 0; t < K; t += 2) {
+            const float2 C = pr2(C4, t);
+            st2(q[N_PPR], t, __ffma2_rn(bn2, pr2(q[N_B], t), pr2(q[N_PMR], t)));
+            st2(q[N_KP], t, __fmul2_rn(C, pr2(gp, t)));
+            st2(q[N_KM], t, __fmul2_rn(C, pr2(gm, t)));
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            q[N_PPR][t] = __fmaf_rn(fd.bn2, q[N_B][t], q[N_PMR][t]);
+            q[N_KP][t] = __fmul_rn(C4[t], gp[t]);
+            q[N_KM][t] = __fmul_rn(C4[t], gm[t]);
+        }
     }
 }
 

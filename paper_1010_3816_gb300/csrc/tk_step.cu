@@ -617,12 +617,16 @@ lw_ring_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__r
 // (the newest level-0 column) level l forms the half node between columns
 // p - l and p - l + 1 and the node p - l, from level l - 1's values at those
 // columns (the one formed at this position and the one kept from the last).
-// Column c's tables are used by level 1 at position c + 1 and by level LV at
-// c + LV, so the ring holds LV + 1 columns: LV in use and one in flight.
-// Every node and half node does the one-step kernel's arithmetic on the same
-// operands (bit-identical to LV single steps).  mask bit l - 1: an outer step
-// ends after level l; off[l - 1]: its sample after the counter's value.
+// Column c's tables (the compact FP32 copy: 16 entries, one bulk copy per
+// column) are used by level 1 at position c + 1 and by level LV at c + LV,
+// and are copied kRingAhead positions before level 1 needs them, so the ring
+// holds LV + kRingAhead columns.  Every node and half node does the one-step
+// kernel's arithmetic on the same operands (the compact tables give the same
+// 21 entries bit for bit), so LV steps are bit-identical to LV single steps.
+// mask bit l - 1: an outer step ends after level l; off[l - 1]: its sample
+// after the counter's value.
 constexpr int kSweepLevels = 4;
+constexpr int kRingAhead = 2;
 
 template <typename T, int K>
 constexpr int multi_warps()
@@ -630,41 +634,44 @@ constexpr int multi_warps()
     return K == 1 ? 16 : K == 2 ? 8 : 4;
 }
 
-template <typename T, int K, int W, int LV>
+template <int LV>
+__host__ __device__ constexpr int multi_slots()
+{
+    return LV + kRingAhead;
+}
+
+template <int K, int W, int LV>
 __host__ __device__ constexpr size_t multi_ring_bytes()
 {
-    return (size_t)W * (LV + 1) * kSlotCols * 32 * K * sizeof(T);
+    return (size_t)W * multi_slots<LV>() * kNCC * 32 * K * sizeof(float);
 }
 
 // the rings, then one mbarrier per ring slot
-template <typename T, int K, int W, int LV>
+template <int K, int W, int LV>
 constexpr size_t multi_smem_bytes()
 {
-    return multi_ring_bytes<T, K, W, LV>() + (size_t)W * (LV + 1) * sizeof(unsigned long long);
+    return multi_ring_bytes<K, W, LV>() + (size_t)W * multi_slots<LV>() * sizeof(unsigned long long);
 }
 
-// Bulk copy of the tables of sweep position p (half_{p-1}, node_{p-1}; the
-// column clamped into the grid, where the values are not used) into the
-// ring slot st.cur, by lane 0.  The slot's previous column was last read at
-// the previous position: the warp's reads are ordered before the copy by the
-// warp barrier and the proxy fence.
-template <typename T, int K, int S>
-__device__ __forceinline__ void ring_issue(T *ring, unsigned long long *bars, RingState &st,
-                                           const T *__restrict__ half, const T *__restrict__ node, int p,
-                                           int Nr, int lane)
+// Bulk copy of the compact tables of sweep position p (column p - 1, clamped
+// into the grid where the values are not used) into the ring slot st.cur, by
+// lane 0.  The slot's previous column was last read at an earlier position:
+// the warp's reads are ordered before the copy by the warp barrier and the
+// proxy fence.
+template <int K, int S>
+__device__ __forceinline__ void ring_issue(float *ring, unsigned long long *bars, RingState &st,
+                                           const float *__restrict__ cmp, int p, int Nr, int lane)
 {
     constexpr int NP = 32 * K;
-    constexpr unsigned HB = kNCH * NP * sizeof(T), NB = kNCN * NP * sizeof(T);
+    constexpr unsigned CB = kNCC * NP * sizeof(float);
     const int s = st.cur;
     __syncwarp();
     if (lane == 0) {
         int c = p - 1;
         c = c < 0 ? 0 : (c > Nr - 1 ? Nr - 1 : c);
-        T *slot = ring + (size_t)s * kSlotCols * NP;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect(bars + s, HB + NB);
-        bulk_fetch(slot, half + (size_t)c * kNCH * NP, HB, bars + s);
-        bulk_fetch(slot + kSlotNode * NP, node + (size_t)c * kNCN * NP, NB, bars + s);
+        mbar_expect(bars + s, CB);
+        bulk_fetch(ring + (size_t)s * kNCC * NP, cmp + (size_t)c * kNCC * NP, CB, bars + s);
     }
     st.issue_ph ^= 1u << s;
     st.cur = s == S - 1 ? 0 : s + 1;
@@ -696,14 +703,16 @@ constexpr size_t multi_obs_scratch_elems_per_warp()
 }
 
 template <typename T, int K, int LV>
-__device__ __forceinline__ void multi_body(T *ring, unsigned long long *bars, RingState &rs, int *err, int i0,
-                                           int i1, int lane, const T *__restrict__ u_in,
-                                           T *__restrict__ u_out, const T *__restrict__ half,
-                                           const T *__restrict__ node, int Nr, T en, int mask,
+__device__ __forceinline__ void multi_body(float *ring, unsigned long long *bars, RingState &rs, int *err,
+                                           int i0, int i1, int lane, const T *__restrict__ u_in,
+                                           T *__restrict__ u_out, const float *__restrict__ cmp,
+                                           const float (&gp)[K], const float (&gm)[K],
+                                           const F32Derive &fd, int Nr, T en, int mask,
                                            const int (&oc)[kObsCols], T *__restrict__ scr)
 {
+    static_assert(sizeof(T) == 4, "the four-step sweep is the FP32 path");
     constexpr int NP = 32 * K;
-    constexpr int S = LV + 1;
+    constexpr int S = multi_slots<LV>();
     constexpr size_t SP = 4 * NP;
     const int row = lane * K;
     T hm[LV][4][K];   // level l + 1: the half node formed at the last position
@@ -714,11 +723,13 @@ __device__ __forceinline__ void multi_body(T *ring, unsigned long long *bars, Ri
         zero_col<T, K>(um[l]);
     }
     const int pa = i0 - LV, pb = i1 + LV - 1;
-    ring_issue<T, K, S>(ring, bars, rs, half, node, pa, Nr, lane);
+    int cur = rs.cur;   // the slot of position pa
+#pragma unroll
+    for (int a = 0; a < kRingAhead; ++a)
+        if (pa + a <= pb) ring_issue<K, S>(ring, bars, rs, cmp, pa + a, Nr, lane);
     T cn[4][K];
     if (pa >= 0) load_state<T, K, true>(u_in + (size_t)pa * SP + row, cn);
     else zero_col<T, K>(cn);
-    int cur = rs.cur == 0 ? S - 1 : rs.cur - 1;   // the slot of position pa
     // the warp's observer columns span [olo, ohi] (olo > ohi: none)
     int olo = 0x7fffffff, ohi = -1;
 #pragma unroll
@@ -730,7 +741,7 @@ __device__ __forceinline__ void multi_body(T *ring, unsigned long long *bars, Ri
     if (!mask) ohi = -1;
     for (int p = pa; p <= pb; ++p) {
         const int nxt = cur == S - 1 ? 0 : cur + 1;
-        if (p + 1 <= pb) ring_issue<T, K, S>(ring, bars, rs, half, node, p + 1, Nr, lane);
+        if (p + kRingAhead <= pb) ring_issue<K, S>(ring, bars, rs, cmp, p + kRingAhead, Nr, lane);
         ring_wait<S>(bars, rs, cur, err);
         T cu[4][K];   // level l - 1 at column p - l + 1
 #pragma unroll
@@ -752,10 +763,18 @@ __device__ __forceinline__ void multi_body(T *ring, unsigned long long *bars, Ri
             const int c = p - l;
             int sl = cur - (l - 1);
             if (sl < 0) sl += S;
-            const T *tab = ring + sl * kSlotCols * NP;   // tables of column c
+            const float *tab = ring + sl * kNCC * NP;   // compact tables of column c
             T hp[4][K], uc[4][K];
-            half_node<T, K>(um[l - 1], cu, tab + row, hp);
-            full_node<T, K>(hm[l - 1], hp, um[l - 1], tab + kSlotNode * NP + row, en, uc);
+            {
+                float q[kNCH][K];
+                derive_half<K>(tab + row, gp, gm, fd, q);
+                half_node_q<T, K>(um[l - 1], cu, q, hp);
+            }
+            {
+                float q[kNCN][K];
+                derive_node<K>(tab + C_B * NP + row, gp, gm, fd, q);
+                full_node_q<T, K>(hm[l - 1], hp, um[l - 1], q, en, uc);
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -785,17 +804,19 @@ __device__ __forceinline__ void multi_body(T *ring, unsigned long long *bars, Ri
 template <typename T, int K, int W, int LV>
 __device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, RingState &rs, int *err,
                                             const T *__restrict__ u_in,
-                                            T *__restrict__ u_out, const T *__restrict__ half,
-                                            const T *__restrict__ node, int Nr, T en,
+                                            T *__restrict__ u_out, const float *__restrict__ cmp,
+                                            const float (&gp)[K], const float (&gm)[K],
+                                            const F32Derive &fd, int Nr, T en,
                                             const WaveArgs &wa, int mask, const int (&off)[LV],
                                             T *__restrict__ scr)
 {
     constexpr int NP = 32 * K;
+    constexpr int S = multi_slots<LV>();
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    T *ring = reinterpret_cast<T *>(sh_raw) + (size_t)wib * (LV + 1) * kSlotCols * NP;
+    float *ring = reinterpret_cast<float *>(sh_raw) + (size_t)wib * S * kNCC * NP;
     unsigned long long *bars =
-        reinterpret_cast<unsigned long long *>(sh_raw + multi_ring_bytes<T, K, W, LV>()) + wib * (LV + 1);
+        reinterpret_cast<unsigned long long *>(sh_raw + multi_ring_bytes<K, W, LV>()) + wib * S;
     int i0, i1, left;
     warp_range<W>(Nr, wib, &i0, &i1, &left);
     if (i1 <= i0) return;
@@ -822,7 +843,8 @@ __device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, RingState &rs
             }
     constexpr size_t kWarpScr = (size_t)kObsCols * LV * 2 * NP;   // per warp
     T *wscr = scr + (size_t)(blockIdx.x * W + wib) * kWarpScr;
-    multi_body<T, K, LV>(ring, bars, rs, err, i0, i1, lane, u_in, u_out, half, node, Nr, en, mask, oc, wscr);
+    multi_body<T, K, LV>(ring, bars, rs, err, i0, i1, lane, u_in, u_out, cmp, gp, gm, fd, Nr, en, mask, oc,
+                         wscr);
     if (n == 0) return;
     const int row = lane * K;
 #pragma unroll
@@ -847,20 +869,24 @@ __device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, RingState &rs
 // an outer step's boundary (k inner steps per outer step).
 template <typename T, int K, int W, int LV>
 __global__ void __launch_bounds__(W * 32, 1)
-lw_multi_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__restrict__ node,
-                           int Nr, T en, const WaveArgs wa, int n_groups, int k, unsigned int *flags,
-                           int *err, T *scr)
+lw_multi_persistent_kernel(T *u0, T *u1, const float *__restrict__ cmp, const float *__restrict__ gpm,
+                           F32Derive fd, int Nr, T en, const WaveArgs wa, int n_groups, int k,
+                           unsigned int *flags, int *err, T *scr)
 {
     extern __shared__ __align__(16) unsigned char sh_raw[];
-    constexpr int S = LV + 1;
+    constexpr int S = multi_slots<LV>();
+    constexpr int NP = 32 * K;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned long long *bars =
-        reinterpret_cast<unsigned long long *>(sh_raw + multi_ring_bytes<T, K, W, LV>()) + wib * S;
+        reinterpret_cast<unsigned long long *>(sh_raw + multi_ring_bytes<K, W, LV>()) + wib * S;
     if (lane == 0) {
         for (int q = 0; q < S; ++q) mbar_init(bars + q);
         mbar_init_fence();
     }
     __syncwarp();
+    float gp[K], gm[K];   // the lane's rows' theta factors of the compact tables
+    ldk<float, K>(gpm + lane * K, gp);
+    ldk<float, K>(gpm + NP + lane * K, gm);
     RingState rs{0, 0u, 0u};
     for (int g = 0; g < n_groups; ++g) {
         const T *in = (g & 1) ? u1 : u0;
@@ -873,7 +899,7 @@ lw_multi_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__
             if (wa.write && (t + l + 1) % k == 0) mask |= 1 << l;
             off[l] = (t + l + 1) / k - 1;
         }
-        multi_sweep<T, K, W, LV>(sh_raw, rs, err, in, out, half, node, Nr, en, wa, mask, off, scr);
+        multi_sweep<T, K, W, LV>(sh_raw, rs, err, in, out, cmp, gp, gm, fd, Nr, en, wa, mask, off, scr);
         if (g + 1 < n_groups && !neighbour_barrier(flags, (unsigned)(g + 1), err)) break;
     }
     // every copy issued has been waited for, unless a wait gave up: then wait
@@ -1155,10 +1181,11 @@ template <typename T, int K, int W>
 cudaError_t launch_multi_persistent_w(const StepLaunch &L, void *u_other, int n_groups, int k,
                                       unsigned int *flags, int *err, void *scratch, cudaStream_t st)
 {
-    constexpr size_t smem = multi_smem_bytes<T, K, W, kSweepLevels>();
+    constexpr size_t smem = multi_smem_bytes<K, W, kSweepLevels>();
     static cudaError_t e0 = cudaFuncSetAttribute(lw_multi_persistent_kernel<T, K, W, kSweepLevels>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e0 != cudaSuccess) return e0;
+    if (!L.cmp || !L.gpm) return cudaErrorInvalidValue;
     WaveArgs wa;
     wa.write = L.write_wave;
     wa.sample = L.sample_ctr;
@@ -1168,11 +1195,12 @@ cudaError_t launch_multi_persistent_w(const StepLaunch &L, void *u_other, int n_
     wa.w_row = L.w_row;
     wa.obs = L.obs;
     T *u0 = (T *)L.u_in, *u1 = (T *)u_other;
-    const T *half = (const T *)L.half, *node = (const T *)L.node;
+    const float *cmp = L.cmp, *gpm = L.gpm;
+    F32Derive fd = f32_derive(L.dt_inner);
     int Nr = L.Nr;
     T en = (T)(0.5 * L.dt_inner);
     T *scr = (T *)scratch;
-    void *args[] = {&u0, &u1, &half, &node, &Nr, &en, &wa, &n_groups, &k, &flags, &err, &scr};
+    void *args[] = {&u0, &u1, &cmp, &gpm, &fd, &Nr, &en, &wa, &n_groups, &k, &flags, &err, &scr};
     return cudaLaunchCooperativeKernel((const void *)lw_multi_persistent_kernel<T, K, W, kSweepLevels>,
                                        dim3(L.blocks), dim3(W * 32), args, smem, st);
 }

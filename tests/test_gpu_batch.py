@@ -1,6 +1,7 @@
-"""Batches (tk_batch_*): many uneven solvers advanced by one persistent kernel
-launch per inner tick, replayed from a CUDA graph, segment length chosen by
-the autotuner.  The batched results must be bit-identical to stepping every
+"""Batches (tk_batch_*): many uneven solvers advanced by one kernel launch per
+inner tick (its warps take work items from a queue in device memory),
+replayed from a CUDA graph, segment length and grid size chosen by the
+autotuner.  The batched results must be bit-identical to stepping every
 member alone (same arithmetic per half node and node), and so inherit the
 members' parity with the oracle, which one member re-checks directly."""
 import math
@@ -93,6 +94,9 @@ def test_autotuner_keeps_state_and_results():
     seg, ms = b.tune(trial_steps=2)
     assert seg in (4, 8, 12, 16, 24, 32, 48, 64, 96, 128) and ms > 0
     assert b.info()["seg"] == seg
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert b.info()["blocks"] % sms == 0 and b.info()["blocks"] >= sms   # the tuned grid
     _same(_results(batched), before)          # tuning left every member untouched
     b.step(5)
     for g, _ in alone:
