@@ -55,6 +55,9 @@ ADJ_FLOP_PER_UPDATE = 2 * 46 + 6 + 10                            # = 108
 ADJ_INSTR_PER_UPDATE = 62
 STATE_BYTES_PER_UPDATE = {0: 64, 1: 32}                         # read u^n, write u^{n+1}
 TABLE_BYTES_PER_UPDATE = {0: 21 * 8, 1: 21 * 4}                 # 11 + 10 table entries
+# the four-step FP32 sweep reads the compact FP32 tables: 16 of the 21 entries
+# per point (the other five are derived in the kernel)
+FP32_SWEEP_TABLE_BYTES = 16 * 4
 NUM_SMS = 152
 FP64_FMA_PER_CLK_PER_SM = 2        # measured: 1.19 TFLOP/s at 1995 MHz on 152 SMs
 FP32_FMA_PER_CLK_PER_SM = 128
@@ -69,9 +72,6 @@ MEASURED_TRAFFIC = {
     # one launch of the one-step kernel: 333.910272 + 37.338880 MB
     ("kerr_a0.9_25601x64_38400steps", 0): (333.910272e6 + 37.338880e6,
                                            "profiles/lw_step_f64_kerr_25601x64.md"),
-    # one launch of 50 sweeps of four steps: 8.628704 + 1.277802 GB
-    ("kerr_a0.9_25601x64_38400steps", 1): ((8.628704000e9 + 1.277802240e9) / 50,
-                                           "profiles/lw_multi_persistent_f32_kerr_25601x64.md"),
 }
 # FP32 on the Kerr workload: every inner step of the solve in one cooperative
 # launch, four Lax-Wendroff steps per sweep over the grid (25601 columns: at
@@ -739,11 +739,11 @@ def measure_solve(args, tk, torch, w, precision, steps, warmup, rank, world, loc
                 "launch_us": kern_s * 1e6}
     else:
         # the unit of work is one sweep of FP32_STEPS_PER_SWEEP inner steps: it
-        # reads u^n and the tables once and writes u^{n+4}; algorithmic bytes
-        # per sweep = (32 + 84) B per point.  All sweeps of the solve run in
-        # one launch.
+        # reads u^n and the compact tables once and writes u^{n+4}; algorithmic
+        # bytes per sweep = (32 + 64) B per point.  All sweeps of the solve run
+        # in one launch.
         sweep_s = spl * kern_s
-        alg = (STATE_BYTES_PER_UPDATE[1] + TABLE_BYTES_PER_UPDATE[1]) * pts
+        alg = (STATE_BYTES_PER_UPDATE[1] + FP32_SWEEP_TABLE_BYTES) * pts
         achieved = alg / sweep_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": HBM_GBS, "unit": "GB/s",
                 "frac": achieved / HBM_GBS, "traffic": traffic,
