@@ -69,9 +69,12 @@ FP32_FMA_PER_CLK_PER_SM = 128
 # keyed by (workload name, precision); the capture's command and figures are in the
 # named summary under profiles/.
 MEASURED_TRAFFIC = {
-    # one launch of the one-step kernel: 333.910272 + 37.338880 MB
-    ("kerr_a0.9_25601x64_38400steps", 0): (333.910272e6 + 37.338880e6,
+    # one launch of the one-step kernel: 334.086400 + 38.545408 MB
+    ("kerr_a0.9_25601x64_38400steps", 0): (334.086400e6 + 38.545408e6,
                                            "profiles/lw_step_f64_kerr_25601x64.md"),
+    # one launch of 50 sweeps of four steps: 6.703077 + 1.271924 GB
+    ("kerr_a0.9_25601x64_38400steps", 1): ((6.703077e9 + 1.271924e9) / 50,
+                                           "profiles/lw_multi_persistent_f32_kerr_25601x64.md"),
 }
 # FP32 on the Kerr workload: every inner step of the solve in one cooperative
 # launch, four Lax-Wendroff steps per sweep over the grid (25601 columns: at
