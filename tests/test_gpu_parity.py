@@ -93,12 +93,14 @@ def test_spin_reversal_is_bitwise_conjugation_on_gpu():
 
 def test_schwarzschild_1601x32_full_run():
     """The 1601 x 32, 2000-step Schwarzschild workload in full.  The s = -2
-    evolution amplifies a 1-ulp change of the initial data to ~3e-11 in Pi by
-    t = 125 M (the oracle disagrees with itself that much), so each quantity
-    is held to max(1e-12, 10 x that sensitivity); waveforms and Phi stay at 1e-12."""
+    evolution amplifies rounding differences to ~2.5e-11 in Pi by t = 125 M:
+    the oracle built with FMA contraction and the oracle from initial data
+    changed by one ulp both differ from the plain oracle by that much, so each
+    quantity is held to max(1e-12, 2 x the larger of the two); waveforms and
+    Phi stay at 1e-12."""
     w = SCHWARZSCHILD_1601x32
     ref = run_oracle(w)
-    res = compare(w, run_gpu(w), ref, perturbed=sensitivity(w))
+    res = compare(w, run_gpu(w), ref, perturbed=[sensitivity(w), run_oracle(w, build="fma")])
     assert res["wave0"] <= 1e-12 and res["PhiR"] <= 1e-12
     print(res)
 
@@ -119,7 +121,7 @@ def test_schwarzschild_1601x32_literal_variable():
     dt <= dr*/8), 400 outer steps; held to the conditioned bar."""
     w = SCHWARZSCHILD_1601x32.with_(variable=0, substeps=4, steps=400)
     ref = run_oracle(w)
-    res = compare(w, run_gpu(w), ref, perturbed=sensitivity(w))
+    res = compare(w, run_gpu(w), ref, perturbed=[sensitivity(w), run_oracle(w, build="fma")])
     print(res)
 
 
