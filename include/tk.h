@@ -97,6 +97,24 @@ tk_status tk_make_grid(tk_solver **out, double rstar_min, double rstar_max, int 
  * Returns TK_ERR_ARG unless M > 0 and |a| < M. */
 tk_status tk_precompute_coeffs(tk_solver *S, double a, double M, int s, int m);
 
+/* Coefficients supplied by the caller instead of computed (the paper leaves
+ * the precompute to its host code): the raw coefficients of the first-order
+ * system (matrices D and S of Eqs. lw1/lw2) in the order b, c1_re, c1_im,
+ * c2_re, c2_im, c3_re, c3_im, c4, c5, at the nodes r*_i (node9) and at the
+ * half nodes r*_{i+1/2} (half9, column i for i < Nr - 1; column Nr - 1 is not
+ * read), each [9][Ntheta][Nr] with r* fastest; for the regularised variable
+ * optionally the angular stencil weights ang2 [2][Ntheta] (A+ toward row
+ * j + 1, then A- toward row j - 1), or NULL to compute them.  They are folded
+ * into the step's tables exactly as tk_precompute_coeffs folds its own.
+ * a, M, s, m are those of tk_precompute_coeffs (w(theta), the stability
+ * bound and the parameter gradients use them; both of the latter evaluate
+ * the library's own coefficients).  Host or device pointers as on_device
+ * says; host inputs go through a temporary device buffer (allocated and
+ * freed; the call synchronizes).  TK_ERR_STATE for a solver made with
+ * substeps = 0; the state must be set again afterwards. */
+tk_status tk_set_coefficients(tk_solver *S, double a, double M, int s, int m, const double *node9,
+                              const double *half9, const double *ang2, int on_device);
+
 /* Initial data (Sec. 3.2).  phi_re, phi_im: planes [Ntheta][Nr] of the evolved
  * field (Phi, or Phi^ = Phi/w in the regularised variable).  pi_re, pi_im: the
  * momentum planes, or both NULL for zero time derivative, Pi = b d_{r*} Phi

@@ -33,7 +33,7 @@ EXPORTS = ("tk_make_grid", "tk_precompute_coeffs", "tk_set_initial_data", "tk_ad
            "tk_batch_set_graph_chunk", "tk_batch_info", "tk_batch_last_error", "tk_batch_destroy",
            "tk_extract_noalloc", "tk_adjoint", "tk_set_initial_gaussian", "tk_get_substeps",
            "tk_set_steps_per_launch", "tk_param_gradient", "tk_check_bounded_wait",
-           "tk_inject_wait_timeout", "tk_probe_fp64_fma")
+           "tk_inject_wait_timeout", "tk_probe_fp64_fma", "tk_set_coefficients")
 
 
 class TkError(RuntimeError):
@@ -92,6 +92,8 @@ def load_library(path: str = LIB_PATH):
                                             C.POINTER(C.c_double)]),
             "tk_check_bounded_wait": (C.c_int, [C.c_int, C.c_int, C.c_int64, _ip]),
             "tk_inject_wait_timeout": (C.c_int, [_vp]),
+            "tk_set_coefficients": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int, C.c_int, _vp, _vp,
+                                              _vp, C.c_int]),
             "tk_probe_fp64_fma": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
                                             C.POINTER(C.c_double)]),
         }
@@ -152,6 +154,18 @@ def tk_make_grid(rstar_min: float, rstar_max: float, Nr: int, Ntheta: int, dt: f
 
 def tk_precompute_coeffs(h, a: float, M: float, s: int, m: int) -> None:
     _check(h, load_library().tk_precompute_coeffs(h, a, M, s, m))
+
+
+def tk_set_coefficients(h, a: float, M: float, s: int, m: int, node9, half9, ang2=None) -> None:
+    """Raw coefficients [9][Ntheta][Nr] at nodes and half nodes (half node i at
+    r*_{i+1/2}) and optionally the regularised stencil [2][Ntheta]; numpy
+    arrays or CUDA tensors (all on the same side)."""
+    p = [_arg(x) for x in (node9, half9, ang2)]
+    dev = {q[1] for q in p if q[1] is not None}
+    if len(dev) != 1:
+        raise ValueError("all arrays must be on the host or all on the device")
+    _check(h, load_library().tk_set_coefficients(h, a, M, int(s), int(m), p[0][0], p[1][0], p[2][0],
+                                                 dev.pop()))
 
 
 def tk_set_initial_data(h, phi_re, phi_im, pi_re=None, pi_im=None) -> None:

@@ -318,6 +318,63 @@ tk_status tk_precompute_coeffs(tk_solver *S, double a, double M, int s, int m)
     return TK_OK;
 }
 
+tk_status tk_set_coefficients(tk_solver *S, double a, double M, int s, int m, const double *node9,
+                              const double *half9, const double *ang2, int on_device)
+{
+    tk_status st = enter(S);
+    if (st != TK_OK) return st;
+    if (!(M > 0) || !isfinite(M) || !(fabs(a) < M))
+        return fail(S, TK_ERR_ARG, "tk_set_coefficients: need M > 0 and |a| < M (a=%g, M=%g)", a, M);
+    if (abs(s) > 4 || abs(m) > 64)
+        return fail(S, TK_ERR_ARG, "tk_set_coefficients: |s| <= 4 and |m| <= 64 required");
+    if (!node9 || !half9) return fail(S, TK_ERR_ARG, "tk_set_coefficients: node9/half9 are NULL");
+    if (S->auto_k)
+        return fail(S, TK_ERR_STATE, "tk_set_coefficients: the solver chooses its own substeps; "
+                                     "make the grid with substeps > 0");
+    S->kerr.M = M;
+    S->kerr.a = a;
+    S->kerr.s = s;
+    S->kerr.m = m;
+    const size_t n9 = (size_t)9 * S->Nth * S->Nr;
+    double *dev = nullptr;   // node9, half9, ang2 on the device (copies of host inputs)
+    const double *dn = node9, *dh = half9;
+    if (!on_device) {
+        st = alloc(S, (void **)&dev, 2 * n9 * sizeof(double));
+        if (st != TK_OK) return st;
+        cudaError_t e = cudaMemcpyAsync(dev, node9, n9 * sizeof(double), cudaMemcpyHostToDevice, S->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dev + n9, half9, n9 * sizeof(double), cudaMemcpyHostToDevice, S->stream);
+        if (e != cudaSuccess) {
+            cudaFree(dev);
+            return fail(S, TK_ERR_CUDA, "tk_set_coefficients: %s", cudaGetErrorString(e));
+        }
+        dn = dev;
+        dh = dev + n9;
+    }
+    cudaError_t e = cudaSuccess;
+    const bool ang_given = (ang2 != nullptr) && S->variable != 0;
+    if (ang_given) {
+        // [2][Ntheta] -> the device layout [2][NP], padding rows zero
+        e = cudaMemsetAsync(S->ang, 0, (size_t)2 * S->NP * sizeof(double), S->stream);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(S->ang + (size_t)k * S->NP, ang2 + (size_t)k * S->Nth, S->Nth * sizeof(double),
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, S->stream);
+    }
+    if (e == cudaSuccess)
+        e = tk::launch_invert_tortoise(S->kerr, S->rs_min, S->drs, S->Nr, S->x_node, S->x_half, S->stream);
+    if (e == cudaSuccess)
+        e = tk::launch_coeff_tables(S->kerr, S->variable, S->Nr, S->Nth, S->NP, S->drs, S->dt / S->substeps,
+                                    S->x_node, S->x_half, S->ang, S->precision, S->half, S->node, S->b_node,
+                                    S->w_row, S->cmp, S->gpm, S->stream, dn, dh, ang_given);
+    if (e == cudaSuccess && dev) e = cudaStreamSynchronize(S->stream);
+    if (dev) cudaFree(dev);
+    if (e != cudaSuccess) return fail(S, TK_ERR_CUDA, "tk_set_coefficients: %s", cudaGetErrorString(e));
+    S->have_coeffs = true;
+    S->have_state = false;
+    S->epoch++;
+    return TK_OK;
+}
+
 tk_status tk_get_substeps(const tk_solver *S, int *substeps)
 {
     if (!S || !substeps) return fail(nullptr, TK_ERR_ARG, "tk_get_substeps: NULL argument");

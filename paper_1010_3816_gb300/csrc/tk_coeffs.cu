@@ -191,6 +191,24 @@ __global__ void regular_stencil_kernel(int s, int m, int Nth, int NP, double *__
     ang[NP + j] = Plo / (Q * dth * dth);
 }
 
+// Raw coefficients supplied by the caller: [9][Nth][Nr] in the order of Raw
+// (b, c1 re/im, c2 re/im, c3 re/im, c4, c5).
+__device__ Raw raw_from(const double *__restrict__ r, int Nth, int Nr, int jp, int i)
+{
+    const size_t plane = (size_t)Nth * Nr, k = (size_t)jp * Nr + i;
+    Raw c;
+    c.b = r[k];
+    c.c1r = r[plane + k];
+    c.c1i = r[2 * plane + k];
+    c.c2r = r[3 * plane + k];
+    c.c2i = r[4 * plane + k];
+    c.c3r = r[5 * plane + k];
+    c.c3i = r[6 * plane + k];
+    c.c4 = r[7 * plane + k];
+    c.c5 = r[8 * plane + k];
+    return c;
+}
+
 template <typename T>
 __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int NP, double drs,
                                     double dt, const double *__restrict__ x_node,
@@ -198,7 +216,9 @@ __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int 
                                     const double *__restrict__ ang, T *__restrict__ half,
                                     T *__restrict__ node, double *__restrict__ b_node,
                                     double *__restrict__ w_row, float *__restrict__ cmp,
-                                    float *__restrict__ gpm, F32Derive fd)
+                                    float *__restrict__ gpm, F32Derive fd,
+                                    const double *__restrict__ raw_node,
+                                    const double *__restrict__ raw_half)
 {
     const int jp = blockIdx.x * blockDim.x + threadIdx.x;
     const int i = blockIdx.y * blockDim.y + threadIdx.y;
@@ -233,7 +253,8 @@ __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int 
             gmv = (jp == 0) ? 0.0 : ith2 - (cs / sn) * i2th;
         }
         {   // node r*_i, Eq. (lw2), step dt
-            const Raw c = raw_coefficients(P, variable, x_node[i], th);
+            const Raw c = raw_node ? raw_from(raw_node, Nth, Nr, jp, i)
+                                   : raw_coefficients(P, variable, x_node[i], th);
             bn = c.b;
             if (i > 0 && i < Nr - 1) {
                 c4n = c.c4;
@@ -268,7 +289,8 @@ __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int 
             }
         }
         if (i < Nr - 1) {   // half node r*_{i+1/2}, Eq. (lw1), step dt/2
-            const Raw c = raw_coefficients(P, variable, x_half[i], th);
+            const Raw c = raw_half ? raw_from(raw_half, Nth, Nr, jp, i)
+                                   : raw_coefficients(P, variable, x_half[i], th);
             c4h = c.c4;
             const double dtau = 0.5 * dt, e2 = 0.5 * dtau;
             const double B = dtau * c.b / drs;
@@ -419,10 +441,11 @@ cudaError_t launch_coeff_tables(const Kerr &P, int variable, int Nr, int Ntheta,
                                 double drs, double dt_inner, const double *x_node,
                                 const double *x_half, double *ang, int precision, void *half,
                                 void *node, double *b_node, double *w_row, float *cmp, float *gpm,
-                                cudaStream_t st)
+                                cudaStream_t st, const double *raw_node, const double *raw_half,
+                                bool ang_given)
 {
     const F32Derive fd = f32_derive(dt_inner);
-    if (variable != 0) {
+    if (variable != 0 && !ang_given) {
         regular_stencil_kernel<<<NP, 32, 0, st>>>(P.s, P.m, Ntheta, NP, ang);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -433,11 +456,12 @@ cudaError_t launch_coeff_tables(const Kerr &P, int variable, int Nr, int Ntheta,
         coeff_tables_kernel<double><<<grid, block, 0, st>>>(P, variable, Nr, Ntheta, NP, drs, dt_inner,
                                                              x_node, x_half, ang, (double *)half,
                                                              (double *)node, b_node, w_row, nullptr,
-                                                             nullptr, fd);
+                                                             nullptr, fd, raw_node, raw_half);
     else
         coeff_tables_kernel<float><<<grid, block, 0, st>>>(P, variable, Nr, Ntheta, NP, drs, dt_inner,
                                                             x_node, x_half, ang, (float *)half,
-                                                            (float *)node, b_node, w_row, cmp, gpm, fd);
+                                                            (float *)node, b_node, w_row, cmp, gpm, fd,
+                                                            raw_node, raw_half);
     return cudaGetLastError();
 }
 

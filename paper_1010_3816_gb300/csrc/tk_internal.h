@@ -106,12 +106,16 @@ struct WaveRead {
 cudaError_t launch_invert_tortoise(const Kerr &P, double rs_min, double drs, int Nr,
                                    double *x_node, double *x_half, cudaStream_t st);
 // FP32 (precision 1) also writes the compact tables cmp and the theta
-// factors gpm[2][NP] (gp, then gm); both may be NULL for FP64.
+// factors gpm[2][NP] (gp, then gm); both may be NULL for FP64.  raw_node,
+// raw_half (device, [9][Ntheta][Nr], half node i at r*_{i+1/2}): coefficients
+// supplied by the caller instead of computed (x_node, x_half then unused);
+// ang_given: ang already holds the regularised stencil.
 cudaError_t launch_coeff_tables(const Kerr &P, int variable, int Nr, int Ntheta, int NP,
                                 double drs, double dt_inner, const double *x_node,
                                 const double *x_half, double *ang, int precision, void *half,
                                 void *node, double *b_node, double *w_row, float *cmp, float *gpm,
-                                cudaStream_t st);
+                                cudaStream_t st, const double *raw_node = nullptr,
+                                const double *raw_half = nullptr, bool ang_given = false);
 
 cudaError_t launch_stiffness(const Kerr &P, int variable, int Nr, int Ntheta, int NP,
                              const double *x_node, const double *ang, unsigned long long *out,

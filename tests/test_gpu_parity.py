@@ -269,3 +269,67 @@ def test_graph_replay_matches_direct_launches():
     for s, wv in out[1:]:
         assert np.array_equal(s, out[0][0])
         assert all(np.array_equal(a, b) for a, b in zip(wv, out[0][1]))
+
+
+def _oracle_coefficients(w):
+    """The oracle's raw coefficient tables in the layout of tk_set_coefficients
+    (half node i at r*_{i+1/2}) and its regularised angular stencil."""
+    import oracle
+    sol = oracle.Solver(M=w.M, a=w.a, s=w.s, m=w.m, rs_min=w.rs_min, rs_max=w.rs_max, Nr=w.Nr,
+                        Ntheta=w.Ntheta, dt=w.dt, substeps=w.substeps, variable=w.variable)
+    node, half = sol.coeffs()
+    half9 = np.zeros_like(half)
+    half9[:, :, :-1] = half[:, :, 1:]
+    ang2 = np.stack(oracle.regular_stencil(w.s, w.m, w.Ntheta)) if w.variable else None
+    return np.ascontiguousarray(node), half9, ang2
+
+
+def run_gpu_with_coefficients(w, node9, half9, ang2, steps=None, precision=0):
+    """run_gpu with the coefficients supplied through tk_set_coefficients."""
+    import torch
+    import paper_1010_3816_gb300 as tk
+    g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
+                  substeps=w.substeps, variable=w.variable, precision=precision)
+    try:
+        tk.tk_set_coefficients(g.h, w.a, w.M, w.s, w.m, node9, half9, ang2)
+        re, im = initial_planes(w)
+        g.set_initial(torch.from_numpy(re).cuda(), torch.from_numpy(im).cuda())
+        ids = [g.add_observer(r, t) for r, t in w.observers]
+        g.step(w.steps if steps is None else steps)
+        return g.state(), [g.waveform(k) for k in ids]
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("kw", [dict(a=0.9, Ntheta=64, noise=1e-3, seed=6),
+                                dict(a=0.7, m=-1, variable=0, Ntheta=32, dt=0.01)])
+def test_parity_with_the_oracles_coefficients(kw):
+    """tk_set_coefficients: the step from the oracle's own coefficient tables
+    (and its angular stencil) matches the oracle at the 1e-12 bar, and differs
+    from the step from the library's precompute only by the rounding of the
+    coefficients."""
+    w = BASE.with_(**kw)
+    node9, half9, ang2 = _oracle_coefficients(w)
+    ref = run_oracle(w)
+    mine = run_gpu_with_coefficients(w, node9, half9, ang2)
+    compare(w, mine, ref)
+    own = run_gpu(w)
+    d = rel_l2(mine[0], own[0])
+    assert 0.0 <= d < 1e-12, d
+
+
+def test_set_coefficients_rejects_bad_calls():
+    import paper_1010_3816_gb300 as tk
+    w = BASE
+    node9, half9, ang2 = _oracle_coefficients(w)
+    g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
+                  substeps=0)
+    with pytest.raises(tk.TkError) as e:            # the solver picks its own substeps
+        tk.tk_set_coefficients(g.h, w.a, w.M, w.s, w.m, node9, half9, ang2)
+    assert e.value.status == tk.TK_ERR_STATE
+    g.close()
+    g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt)
+    with pytest.raises(tk.TkError) as e:
+        tk.tk_set_coefficients(g.h, 1.0, 1.0, w.s, w.m, node9, half9, ang2)    # |a| = M
+    assert e.value.status == tk.TK_ERR_ARG
+    g.close()
