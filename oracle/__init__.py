@@ -122,6 +122,8 @@ def _lib(variant: str = "plain"):
             lib.tko_get_state.argtypes = [C.c_void_p, _dp]
             lib.tko_replace_state.restype = None
             lib.tko_replace_state.argtypes = [C.c_void_p, _dp]
+            lib.tko_replace_coeffs.restype = None
+            lib.tko_replace_coeffs.argtypes = [C.c_void_p, _dp, _dp]
             lib.tko_add_observer.restype = C.c_int
             lib.tko_add_observer.argtypes = [C.c_void_p, C.c_double, C.c_double]
             lib.tko_run.restype = None
@@ -273,6 +275,13 @@ class Solver:
         """Overwrite the state (4 planes), keeping steps and samples."""
         a = np.ascontiguousarray(planes4, dtype=np.float64).reshape(4, self.Ntheta, self.Nr)
         self._lib.tko_replace_state(self._h, _ptr(a))
+
+    def replace_coeffs(self, node, half) -> None:
+        """Overwrite the coefficient tables (layout of ``coeffs()``)."""
+        shp = (NCOEF, self.Ntheta, self.Nr)
+        n = np.ascontiguousarray(node, dtype=np.float64).reshape(shp)
+        h = np.ascontiguousarray(half, dtype=np.float64).reshape(shp)
+        self._lib.tko_replace_coeffs(self._h, _ptr(n), _ptr(h))
 
     def coeffs(self):
         """(node, half) coefficient tables, each [NCOEF][Ntheta][Nr]; the half

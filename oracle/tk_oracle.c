@@ -436,6 +436,15 @@ void tko_replace_state(tko_state *S, const double *in4)
     for (int k = 0; k < 4; ++k) memcpy(S->q[k], in4 + k * plane, plane * sizeof(double));
 }
 
+/* Overwrite the coefficient tables (layout of tko_get_coeffs; tests only:
+ * the conditioning of a run under a change of its coefficients). */
+void tko_replace_coeffs(tko_state *S, const double *node, const double *half)
+{
+    size_t n = (size_t)NCOEF * S->p.Nr * S->p.Ntheta;
+    memcpy(S->coef_node, node, n * sizeof(double));
+    memcpy(S->coef_half, half, n * sizeof(double));
+}
+
 /* ------------------------------------------------------------------------ */
 /* The right-hand side in the square brackets of Eqs. (lw1)/(lw2):           */
 /*     (1/dr*) D (u_right - u_left) - S(u_avg)                               */

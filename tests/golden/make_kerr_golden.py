@@ -8,7 +8,12 @@ each full physical plane.  Takes about two hours on 6 cores.
 
 With --fma it writes kerr_25601x64_oracle_fma.npz: the same run through the
 same oracle source compiled with FMA contraction (oracle.Solver(build="fma")),
-a second correct rounding order of the scheme.
+a second correct rounding order of the scheme.  With --coeffs it writes
+kerr_25601x64_oracle_coeffs.npz: the run with every coefficient of the tables
+multiplied by 1 + 4.4e-16 * N(0, 1) (seed 12347), i.e. changed by about two
+ulps, the size of the differences between two correct FP64 evaluations of the
+coefficient formulas (their transcendental functions are not correctly
+rounded); stored on every 8th theta row and 16th r* column.
 
 With --perturbed it writes kerr_25601x64_oracle_perturbed.npz instead: the same
 run from the real initial plane times 1 + 2.2e-16 * N(0, 1) (numpy's default
@@ -22,7 +27,7 @@ differences two correct implementations accumulate.  The differences of these
 runs from the plain one are the run's own conditioning, which sets the parity
 bar of the full-length test.
 
-    python tests/golden/make_kerr_golden.py [threads] [--perturbed | --noisy | --fma]
+    python tests/golden/make_kerr_golden.py [threads] [--perturbed | --noisy | --fma | --coeffs]
 """
 import math
 import os
@@ -48,6 +53,7 @@ EPS = 2.2e-16
 SEED = 12345
 NOISE_EVERY = 16                 # outer steps between the noisy run's perturbations
 NOISE_EPS = 4 * EPS              # sqrt(16) ulps: one ulp per outer step as a random walk
+COEF_EPS = 2 * EPS               # about two ulps of every coefficient
 
 
 def main():
@@ -55,8 +61,9 @@ def main():
     perturbed = "--perturbed" in sys.argv
     noisy = "--noisy" in sys.argv
     fma = "--fma" in sys.argv
-    assert perturbed + noisy + fma <= 1, "one variant at a time"
-    rows, cols = (SPARSE_ROWS, SPARSE_COLS) if (perturbed or noisy) else (ROWS, COLS)
+    coeffs = "--coeffs" in sys.argv
+    assert perturbed + noisy + fma + coeffs <= 1, "one variant at a time"
+    rows, cols = (SPARSE_ROWS, SPARSE_COLS) if (perturbed or noisy or coeffs) else (ROWS, COLS)
     if args:
         oracle.set_threads(int(args[0]))
     w = KERR_25601x64
@@ -64,6 +71,11 @@ def main():
                         Ntheta=w.Ntheta, dt=w.dt, substeps=w.substeps, variable=w.variable,
                         build="fma" if fma else "plain")
     ids = [sol.add_observer(r, t) for r, t in w.observers]
+    if coeffs:
+        node, half = sol.coeffs()
+        crng = np.random.default_rng(SEED + 2)
+        sol.replace_coeffs(node * (1.0 + COEF_EPS * crng.standard_normal(node.shape)),
+                           half * (1.0 + COEF_EPS * crng.standard_normal(half.shape)))
     re, im = initial_planes(w)
     if perturbed:
         re = re * (1.0 + EPS * np.random.default_rng(SEED).standard_normal(re.shape))
@@ -87,7 +99,8 @@ def main():
     phys = st * wt
     np.savez_compressed(
         os.path.join(HERE, "kerr_25601x64_oracle" + ("_perturbed" if perturbed else "")
-                     + ("_noisy" if noisy else "") + ("_fma" if fma else "") + ".npz"),
+                     + ("_noisy" if noisy else "") + ("_fma" if fma else "")
+                     + ("_coeffs" if coeffs else "") + ".npz"),
         wave0=sol.waveform(ids[0]), wave1=sol.waveform(ids[1]),
         state_sub=phys[:, rows, cols], plane_norms=np.linalg.norm(phys.reshape(4, -1), axis=1),
         rows=np.arange(w.Ntheta)[rows], cols=np.arange(w.Nr)[cols],
@@ -95,7 +108,8 @@ def main():
                       + (f", real initial plane times 1 + {EPS} N(0,1), seed {SEED}" if perturbed else "")
                       + (f", state times 1 + {NOISE_EPS} N(0,1) every {NOISE_EVERY} outer steps, seed "
                          f"{SEED + 1}" if noisy else "")
-                      + (", oracle compiled with FMA contraction" if fma else "")))
+                      + (", oracle compiled with FMA contraction" if fma else "")
+                      + (f", coefficients times 1 + {COEF_EPS} N(0,1), seed {SEED + 2}" if coeffs else "")))
 
 
 if __name__ == "__main__":

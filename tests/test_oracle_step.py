@@ -355,3 +355,26 @@ def test_fma_build_is_another_rounding_of_the_same_scheme():
     d = np.linalg.norm(s1 - s0) / np.linalg.norm(s0)
     dw = np.linalg.norm(w1 - w0) / np.linalg.norm(w0)
     assert 0.0 < d < 1e-12 and dw < 1e-12, (d, dw)
+
+
+def test_replace_coeffs_round_trip():
+    """replace_coeffs writes exactly what coeffs() reads, and a run with the
+    tables put back unchanged is bit-identical to one never touched."""
+    import math
+    import oracle
+    from inputs import Workload, initial_planes
+    w = Workload(name="rc", a=0.7, rs_min=-20.0, rs_max=30.0, Nr=201, Ntheta=8, dt=0.125, steps=20,
+                 center=3.0, width=2.0, observers=((10.0, math.pi / 2),))
+    out = []
+    for touch in (False, True):
+        sol = oracle.Solver(M=w.M, a=w.a, s=w.s, m=w.m, rs_min=w.rs_min, rs_max=w.rs_max, Nr=w.Nr,
+                            Ntheta=w.Ntheta, dt=w.dt, substeps=w.substeps, variable=w.variable)
+        if touch:
+            node, half = sol.coeffs()
+            sol.replace_coeffs(node.copy(), half.copy())
+            n2, h2 = sol.coeffs()
+            assert np.array_equal(n2, node) and np.array_equal(h2, half)
+        sol.set_initial(*initial_planes(w))
+        sol.run(w.steps)
+        out.append(sol.state())
+    assert np.array_equal(out[0], out[1])
