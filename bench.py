@@ -14,7 +14,7 @@ region, and the CPU oracle timed on a bounded sample on the host cores.
 ``--impl reference`` times the CPU oracle instead (each step a bounded sample
 of the same workload) and prints the same line with ``"impl": "reference"``.
 
-Multi-GPU (torchrun): the solve does not shard in this build; each rank runs
+Multi-GPU (torchrun): one solve is not split across GPUs; each rank runs
 its own replica of the workload and ``value`` counts the updates of all ranks
 over the slowest rank's time.
 """
