@@ -115,6 +115,15 @@ tk_status tk_precompute_coeffs(tk_solver *S, double a, double M, int s, int m);
 tk_status tk_set_coefficients(tk_solver *S, double a, double M, int s, int m, const double *node9,
                               const double *half9, const double *ang2, int on_device);
 
+/* The raw coefficients of the library's own precompute for the current
+ * (a, M, s, m), in the layout of tk_set_coefficients (half9 column Nr - 1 is
+ * zero), evaluated again from the stored r(r*) inversion; for inspecting or
+ * exporting the precompute (the paper leaves it to its host code).  Host or
+ * device buffers of 9 * Ntheta * Nr doubles each; a host read-out allocates
+ * and frees a temporary device buffer and synchronizes.  TK_ERR_STATE before
+ * tk_precompute_coeffs. */
+tk_status tk_get_coefficients(tk_solver *S, double *node9, double *half9, int on_device);
+
 /* Initial data (Sec. 3.2).  phi_re, phi_im: planes [Ntheta][Nr] of the evolved
  * field (Phi, or Phi^ = Phi/w in the regularised variable).  pi_re, pi_im: the
  * momentum planes, or both NULL for zero time derivative, Pi = b d_{r*} Phi

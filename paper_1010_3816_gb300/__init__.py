@@ -33,7 +33,8 @@ EXPORTS = ("tk_make_grid", "tk_precompute_coeffs", "tk_set_initial_data", "tk_ad
            "tk_batch_set_graph_chunk", "tk_batch_info", "tk_batch_last_error", "tk_batch_destroy",
            "tk_extract_noalloc", "tk_adjoint", "tk_set_initial_gaussian", "tk_get_substeps",
            "tk_set_steps_per_launch", "tk_param_gradient", "tk_check_bounded_wait",
-           "tk_inject_wait_timeout", "tk_probe_fp64_fma", "tk_set_coefficients")
+           "tk_inject_wait_timeout", "tk_probe_fp64_fma", "tk_set_coefficients",
+           "tk_get_coefficients")
 
 
 class TkError(RuntimeError):
@@ -94,6 +95,7 @@ def load_library(path: str = LIB_PATH):
             "tk_inject_wait_timeout": (C.c_int, [_vp]),
             "tk_set_coefficients": (C.c_int, [_vp, C.c_double, C.c_double, C.c_int, C.c_int, _vp, _vp,
                                               _vp, C.c_int]),
+            "tk_get_coefficients": (C.c_int, [_vp, _vp, _vp, C.c_int]),
             "tk_probe_fp64_fma": (C.c_int, [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
                                             C.POINTER(C.c_double)]),
         }
@@ -166,6 +168,14 @@ def tk_set_coefficients(h, a: float, M: float, s: int, m: int, node9, half9, ang
         raise ValueError("all arrays must be on the host or all on the device")
     _check(h, load_library().tk_set_coefficients(h, a, M, int(s), int(m), p[0][0], p[1][0], p[2][0],
                                                  dev.pop()))
+
+
+def tk_get_coefficients(h, shape):
+    """(node9, half9): the precompute's raw coefficients, numpy [9][Ntheta][Nr]."""
+    node = np.zeros((9,) + tuple(shape))
+    half = np.zeros((9,) + tuple(shape))
+    _check(h, load_library().tk_get_coefficients(h, node.ctypes.data, half.ctypes.data, 0))
+    return node, half
 
 
 def tk_set_initial_data(h, phi_re, phi_im, pi_re=None, pi_im=None) -> None:

@@ -375,6 +375,31 @@ tk_status tk_set_coefficients(tk_solver *S, double a, double M, int s, int m, co
     return TK_OK;
 }
 
+tk_status tk_get_coefficients(tk_solver *S, double *node9, double *half9, int on_device)
+{
+    tk_status st = enter(S);
+    if (st != TK_OK) return st;
+    if (!S->have_coeffs) return fail(S, TK_ERR_STATE, "tk_get_coefficients before tk_precompute_coeffs");
+    if (!node9 || !half9) return fail(S, TK_ERR_ARG, "tk_get_coefficients: node9/half9 are NULL");
+    const size_t n9 = (size_t)9 * S->Nth * S->Nr;
+    if (on_device) {
+        TK_CUDA(S, tk::launch_raw_export(S->kerr, S->variable, S->Nr, S->Nth, S->x_node, S->x_half, node9,
+                                         half9, S->stream));
+        return TK_OK;
+    }
+    double *dev = nullptr;
+    st = alloc(S, (void **)&dev, 2 * n9 * sizeof(double));
+    if (st != TK_OK) return st;
+    cudaError_t e = tk::launch_raw_export(S->kerr, S->variable, S->Nr, S->Nth, S->x_node, S->x_half, dev,
+                                          dev + n9, S->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(node9, dev, n9 * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(half9, dev + n9, n9 * sizeof(double), cudaMemcpyDeviceToHost, S->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+    cudaFree(dev);
+    if (e != cudaSuccess) return fail(S, TK_ERR_CUDA, "tk_get_coefficients: %s", cudaGetErrorString(e));
+    return TK_OK;
+}
+
 tk_status tk_get_substeps(const tk_solver *S, int *substeps)
 {
     if (!S || !substeps) return fail(nullptr, TK_ERR_ARG, "tk_get_substeps: NULL argument");

@@ -10,6 +10,7 @@
 //    dt, dr*, dtheta into the step kernel's tables, and the angular boundary
 //    conditions of Sec. 3.2 are folded into the first and last theta rows.
 #include <math.h>
+#include <algorithm>
 
 #include "tk_internal.h"
 
@@ -384,6 +385,29 @@ __global__ void coeff_tables_kernel(Kerr KP, int variable, int Nr, int Nth, int 
     b_node[(size_t)i * NP + jp] = bn;
 }
 
+// The raw coefficients the precompute forms, [9][Nth][Nr] in the order of Raw,
+// at the nodes and (column i < Nr - 1) the half nodes r*_{i+1/2}; column
+// Nr - 1 of the half table is zero.  Grid-stride over the Nth * Nr points.
+__global__ void raw_export_kernel(Kerr KP, int variable, int Nr, int Nth,
+                                  const double *__restrict__ x_node, const double *__restrict__ x_half,
+                                  double *__restrict__ out_node, double *__restrict__ out_half)
+{
+    const Geo P = geometry(KP);
+    const size_t plane = (size_t)Nth * Nr;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < plane;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const int jp = (int)(k / Nr), i = (int)(k % Nr);
+        const double th = (jp + 0.5) * (M_PI / Nth);
+        const Raw c = raw_coefficients(P, variable, x_node[i], th);
+        const double v[9] = {c.b, c.c1r, c.c1i, c.c2r, c.c2i, c.c3r, c.c3i, c.c4, c.c5};
+        for (int q = 0; q < 9; ++q) out_node[q * plane + k] = v[q];
+        Raw h = {};
+        if (i < Nr - 1) h = raw_coefficients(P, variable, x_half[i], th);
+        const double w[9] = {h.b, h.c1r, h.c1i, h.c2r, h.c2i, h.c3r, h.c3i, h.c4, h.c5};
+        for (int q = 0; q < 9; ++q) out_half[q * plane + k] = w[q];
+    }
+}
+
 // Stiffness of the source term at every interior node: a Gershgorin bound on
 // the spectrum of the Phi -> Pi coupling c3 + c4 (angular stencil), i.e. on
 // omega^2 of the fastest angular oscillation, and the radial speed b.  The two
@@ -426,6 +450,15 @@ cudaError_t launch_stiffness(const Kerr &P, int variable, int Nr, int Ntheta, in
     if (e != cudaSuccess) return e;
     dim3 block(32, 8), grid((NP + 31) / 32, (Nr + 7) / 8);
     stiffness_kernel<<<grid, block, 0, st>>>(P, variable, Nr, Ntheta, NP, x_node, ang, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raw_export(const Kerr &P, int variable, int Nr, int Ntheta, const double *x_node,
+                              const double *x_half, double *out_node, double *out_half, cudaStream_t st)
+{
+    const size_t n = (size_t)Ntheta * Nr;
+    const int blocks = (int)std::min<size_t>((n + 255) / 256, 152 * 8);
+    raw_export_kernel<<<blocks, 256, 0, st>>>(P, variable, Nr, Ntheta, x_node, x_half, out_node, out_half);
     return cudaGetLastError();
 }
 

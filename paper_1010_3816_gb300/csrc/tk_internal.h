@@ -117,6 +117,11 @@ cudaError_t launch_coeff_tables(const Kerr &P, int variable, int Nr, int Ntheta,
                                 cudaStream_t st, const double *raw_node = nullptr,
                                 const double *raw_half = nullptr, bool ang_given = false);
 
+// The raw coefficients of the precompute, [9][Ntheta][Nr] at nodes and half
+// nodes (device output buffers).
+cudaError_t launch_raw_export(const Kerr &P, int variable, int Nr, int Ntheta, const double *x_node,
+                              const double *x_half, double *out_node, double *out_half, cudaStream_t st);
+
 cudaError_t launch_stiffness(const Kerr &P, int variable, int Nr, int Ntheta, int NP,
                              const double *x_node, const double *ang, unsigned long long *out,
                              cudaStream_t st);

@@ -333,3 +333,43 @@ def test_set_coefficients_rejects_bad_calls():
         tk.tk_set_coefficients(g.h, 1.0, 1.0, w.s, w.m, node9, half9, ang2)    # |a| = M
     assert e.value.status == tk.TK_ERR_ARG
     g.close()
+
+
+@pytest.mark.parametrize("kw", [dict(a=0.9, Ntheta=64, noise=1e-3, seed=6),
+                                dict(a=0.7, m=-1, variable=0, Ntheta=32, dt=0.01),
+                                dict(a=0.9, rs_min=-100.0, rs_max=40.0, Nr=1121, Ntheta=16, steps=40,
+                                     observers=((30.0, math.pi / 2), (-90.0, 1.0)))])
+def test_get_coefficients_round_trip_and_oracle_agreement(kw):
+    """tk_get_coefficients exports the precompute's raw coefficients: they are
+    the oracle's to FP64 evaluation error (c1R, which cancels near the horizon
+    and far out, only where it does not), and fed back through
+    tk_set_coefficients they reproduce the default run bit for bit (the fold is
+    the same code from the same values)."""
+    import paper_1010_3816_gb300 as tk
+    w = BASE.with_(**kw)
+    g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
+                  substeps=w.substeps, variable=w.variable)
+    with pytest.raises(tk.TkError) as e:
+        tk.tk_get_coefficients(g.h, (w.Ntheta, w.Nr))
+    assert e.value.status == tk.TK_ERR_STATE              # before the precompute
+    g.precompute(w.a, w.M, w.s, w.m)
+    node9, half9 = tk.tk_get_coefficients(g.h, (w.Ntheta, w.Nr))
+    g.close()
+    assert np.all(half9[:, :, -1] == 0)
+    on, oh9, _ = _oracle_coefficients(w)
+    rs = w.rs_min + np.arange(w.Nr) * w.drs
+    import oracle
+    for mine, ref in ((node9, on), (half9, oh9)):
+        for q, name in enumerate(oracle.COEF_NAMES):
+            colmax = np.abs(ref[q]).max(axis=0, keepdims=True)
+            d = np.abs(mine[q] - ref[q]) / np.where(colmax > 0, colmax, 1.0)
+            if name == "c1R":
+                d = d[:, (rs > -30.0) & (rs < 60.0)]
+                assert d.max() < 1e-9, name
+            else:
+                assert d.max() < 1e-10, (name, d.max())
+    mine = run_gpu_with_coefficients(w, node9, half9, None)
+    own = run_gpu(w)
+    assert np.array_equal(mine[0], own[0])
+    for a, b in zip(mine[1], own[1]):
+        assert np.array_equal(a, b)
