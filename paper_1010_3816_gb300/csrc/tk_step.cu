@@ -109,7 +109,7 @@ __device__ __forceinline__ void load_state(const T *p, T (&u)[4][K])
 // half node, the others receive it through shared memory after a block
 // barrier.  write: observe this step; sample_offset: samples after the
 // counter's value.
-template <typename T, int K, int W, bool CG>
+template <typename T, int K, int W>
 __device__ __forceinline__ void step_sweep(unsigned char *sh_raw, const T *__restrict__ u_in,
                                            T *__restrict__ u_out,
                                            const T *__restrict__ half, const T *__restrict__ node,
@@ -130,10 +130,10 @@ __device__ __forceinline__ void step_sweep(unsigned char *sh_raw, const T *__res
 
     T ua[4][K], hm[4][K];
     if (i1 > i0) {
-        load_state<T, K, CG>(u_in + (size_t)i0 * SP + row, ua);
+        load_state<T, K, false>(u_in + (size_t)i0 * SP + row, ua);
         if (lead && i0 > 0) {
             T ul[4][K];
-            load_state<T, K, CG>(u_in + (size_t)(i0 - 1) * SP + row, ul);
+            load_state<T, K, false>(u_in + (size_t)(i0 - 1) * SP + row, ul);
             half_node<T, K>(ul, ua, half + (size_t)(i0 - 1) * HP + row, hm);
         } else {
             zero_col<T, K>(hm);
@@ -141,7 +141,7 @@ __device__ __forceinline__ void step_sweep(unsigned char *sh_raw, const T *__res
         for (int i = i0; i < i1; ++i) {
             T uc[4][K], hp[4][K], o[4][K];
             if (i + 1 < Nr) {
-                load_state<T, K, CG>(u_in + (size_t)(i + 1) * SP + row, uc);
+                load_state<T, K, false>(u_in + (size_t)(i + 1) * SP + row, uc);
                 half_node<T, K>(ua, uc, half + (size_t)i * HP + row, hp);
             } else {
                 zero_col<T, K>(uc);
@@ -203,16 +203,17 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
 {
     extern __shared__ __align__(16) unsigned char sh_raw[];
     if (kUsePDL) chain_start();
-    step_sweep<T, K, W, false>(sh_raw, u_in, u_out, half, node, Nr, eh, en, wa, wa.write, 0);
+    step_sweep<T, K, W>(sh_raw, u_in, u_out, half, node, Nr, eh, en, wa, wa.write, 0);
     if (wa.write) advance_sample(wa);
 }
 
 // Many Lax-Wendroff steps in one launch, for grids too small to fill the GPU
 // with long sweeps, where per-launch overhead would dominate.  All blocks are
 // resident at once (cooperative launch).  After each step a block publishes
-// the step count in flags[block] and waits until both neighbouring blocks
-// have published it: the next step reads one column of u from each of them,
-// and overwrites the level they read in this step.  Every wait is bounded:
+// the step count in flags[block]; in the next step it waits until both
+// neighbouring blocks have published it before it touches the columns that
+// involve them (it reads one column of u from each, and overwrites the level
+// they read in the step before; step_sweep_split).  Every wait is bounded:
 // after kMaxSpins polls the block sets *err and every block leaves its loop
 // (the state is then invalid and the host reports the error).  State loads go
 // through L2 (other blocks write them).  u0 holds u^n at the start; the result
@@ -254,20 +255,190 @@ __device__ __forceinline__ bool neighbour_barrier(unsigned int *flags, unsigned 
     return ok != 0;
 }
 
+// Split form of the neighbour barrier for the persistent one-step sweep: a
+// block publishes that its previous step is complete, forms the part of the
+// next step that needs nothing from its neighbours, and only then waits for
+// them (bounded, as neighbour_barrier).
+__device__ __forceinline__ void publish_epoch(unsigned int *flags, unsigned int epoch)
+{
+    __syncthreads();                       // the block's stores of the last step are issued
+    if (threadIdx.x == 0) {
+        __threadfence();                   // and visible to the other blocks
+        atomicExch(&flags[blockIdx.x], epoch);
+    }
+}
+
+__device__ __forceinline__ bool wait_neighbours(unsigned int *flags, unsigned int epoch, int *err)
+{
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        int good = 1;
+        for (int side = -1; side <= 1 && good; side += 2) {
+            const int nb = (int)blockIdx.x + side;
+            if (nb < 0 || nb >= (int)gridDim.x) continue;
+            long long spins = 0;
+            while (load_acquire(&flags[nb]) < epoch) {
+                if (++spins > kMaxSpins || *(volatile int *)err) {
+                    good = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (!good) atomicExch(err, 1);
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// One step of the persistent sweep in two phases around the wait for the
+// neighbouring blocks.  Before it: every node and half node that reads and
+// writes only this block's columns (u^n of the block's columns was written by
+// this block in the previous step).  After it: the block's first column (its
+// left half node reads the left neighbour's last column) and its last column
+// (its right half node reads the right neighbour's first column), which are
+// also the only columns of u^n the neighbours read, so they are overwritten
+// only once the neighbours have finished their previous step; and the first
+// node of every warp, deferred as in step_sweep.  Same arithmetic on the same
+// operands as step_sweep.
+template <typename T, int K, int W>
+__device__ __forceinline__ bool step_sweep_split(unsigned char *sh_raw, const T *__restrict__ u_in,
+                                                 T *__restrict__ u_out, const T *__restrict__ half,
+                                                 const T *__restrict__ node, int Nr, T en,
+                                                 const WaveArgs &wa, int write, int sample_offset,
+                                                 unsigned int *flags, unsigned int epoch, int *err)
+{
+    constexpr int NP = 32 * K;
+    constexpr size_t SP = 4 * NP, HP = (size_t)kNCH * NP, NQ = (size_t)kNCN * NP;
+    T(*sh)[3][4][NP] = reinterpret_cast<T(*)[3][4][NP]>(sh_raw);
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int i0, i1, left;
+    warp_range<W>(Nr, wib, &i0, &i1, &left);
+    const int row = lane * K;
+    const bool lead = (left < 0);
+    const int b1 = (int)(((long long)(blockIdx.x + 1) * Nr) / gridDim.x);
+    const bool last = (i1 > i0) && (i1 == b1);
+    const int iend = last ? i1 - 1 : i1;
+    T ua[4][K], hm[4][K];
+    zero_col<T, K>(hm);
+    if (i1 > i0) {
+        load_state<T, K, true>(u_in + (size_t)i0 * SP + row, ua);
+        for (int i = i0; i < iend; ++i) {
+            T uc[4][K], hp[4][K], o[4][K];
+            if (i + 1 < Nr) {
+                load_state<T, K, true>(u_in + (size_t)(i + 1) * SP + row, uc);
+                half_node<T, K>(ua, uc, half + (size_t)i * HP + row, hp);
+            } else {
+                zero_col<T, K>(uc);
+                zero_col<T, K>(hp);
+            }
+            if (i == i0) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+#pragma unroll
+                    for (int t = 0; t < K; ++t) {
+                        sh[wib][1][c][row + t] = ua[c][t];
+                        sh[wib][2][c][row + t] = hp[c][t];
+                    }
+            } else {
+                full_node<T, K>(hm, hp, ua, node + (size_t)i * NQ + row, en, o);
+                if (i == 0 || i == Nr - 1) zero_col<T, K>(o);
+                store_col<T, K>(u_out + (size_t)i * SP + row, o);
+                if (write)
+                    observe<T, K>(i, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, sample_offset);
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    hm[c][t] = hp[c][t];
+                    ua[c][t] = uc[c][t];
+                }
+        }
+        if (!last)   // u^{n+1/2} at i1 - 1/2: the right neighbour warp's left half node
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int t = 0; t < K; ++t) sh[wib][0][c][row + t] = hm[c][t];
+    }
+    if (epoch > 0) {
+        if (!wait_neighbours(flags, epoch, err)) return false;
+    } else {
+        __syncthreads();
+    }
+    if (last) {
+        const int i = i1 - 1;
+        T uc[4][K], hp[4][K];
+        if (i + 1 < Nr) {
+            load_state<T, K, true>(u_in + (size_t)(i + 1) * SP + row, uc);
+            half_node<T, K>(ua, uc, half + (size_t)i * HP + row, hp);
+        } else {
+            zero_col<T, K>(uc);
+            zero_col<T, K>(hp);
+        }
+        if (i == i0) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int t = 0; t < K; ++t) {
+                    sh[wib][1][c][row + t] = ua[c][t];
+                    sh[wib][2][c][row + t] = hp[c][t];
+                }
+        } else {
+            T o[4][K];
+            full_node<T, K>(hm, hp, ua, node + (size_t)i * NQ + row, en, o);
+            if (i == 0 || i == Nr - 1) zero_col<T, K>(o);
+            store_col<T, K>(u_out + (size_t)i * SP + row, o);
+            if (write) observe<T, K>(i, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, sample_offset);
+        }
+    }
+    if (i1 > i0) {
+        T hl[4][K], uf[4][K], hf[4][K], o[4][K];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+                uf[c][t] = sh[wib][1][c][row + t];
+                hf[c][t] = sh[wib][2][c][row + t];
+            }
+        if (lead) {
+            if (i0 > 0) {
+                T ul[4][K];
+                load_state<T, K, true>(u_in + (size_t)(i0 - 1) * SP + row, ul);
+                half_node<T, K>(ul, uf, half + (size_t)(i0 - 1) * HP + row, hl);
+            } else {
+                zero_col<T, K>(hl);
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+#pragma unroll
+                for (int t = 0; t < K; ++t) hl[c][t] = sh[left][0][c][row + t];
+        }
+        full_node<T, K>(hl, hf, uf, node + (size_t)i0 * NQ + row, en, o);
+        if (i0 == 0 || i0 == Nr - 1) zero_col<T, K>(o);
+        store_col<T, K>(u_out + (size_t)i0 * SP + row, o);
+        if (write) observe<T, K>(i0, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, sample_offset);
+    }
+    return true;
+}
+
 template <typename T, int K, int W>
 __global__ void __launch_bounds__(W * 32, wide_warps<T, K>() / W)
 lw_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__restrict__ node, int Nr,
-                     T eh, T en, const WaveArgs wa, int n_inner, int substeps, unsigned int *flags,
-                     int *err)
+                     T en, const WaveArgs wa, int n_inner, int substeps, unsigned int *flags, int *err)
 {
     extern __shared__ __align__(16) unsigned char sh_raw[];
     for (int s = 0; s < n_inner; ++s) {
         const T *in = (s & 1) ? u1 : u0;
         T *out = (s & 1) ? u0 : u1;
         const int write = wa.write && ((s + 1) % substeps == 0);
-        step_sweep<T, K, W, true>(sh_raw, in, out, half, node, Nr, eh, en, wa, write,
-                                  (s + 1) / substeps - 1);
-        if (s + 1 < n_inner && !neighbour_barrier(flags, (unsigned)(s + 1), err)) break;
+        if (s > 0) publish_epoch(flags, (unsigned)s);
+        if (!step_sweep_split<T, K, W>(sh_raw, in, out, half, node, Nr, en, wa, write, (s + 1) / substeps - 1,
+                                       flags, (unsigned)s, err))
+            break;
     }
     if (wa.write) advance_sample(wa, n_inner / substeps);
 }
@@ -1107,8 +1278,8 @@ cudaError_t launch_persistent_w(const StepLaunch &L, void *u_other, int n_inner,
     T *u0 = (T *)L.u_in, *u1 = (T *)u_other;
     const T *half = (const T *)L.half, *node = (const T *)L.node;
     int Nr = L.Nr;
-    T eh = (T)(0.25 * L.dt_inner), en = (T)(0.5 * L.dt_inner);
-    void *args[] = {&u0, &u1, &half, &node, &Nr, &eh, &en, &wa, &n_inner, &substeps, &flags, &err};
+    T en = (T)(0.5 * L.dt_inner);
+    void *args[] = {&u0, &u1, &half, &node, &Nr, &en, &wa, &n_inner, &substeps, &flags, &err};
     return cudaLaunchCooperativeKernel((const void *)lw_persistent_kernel<T, K, W>, dim3(L.blocks),
                                        dim3(W * 32), args, step_smem_bytes<T, K, W>(), st);
 }
