@@ -13,7 +13,12 @@ kerr_25601x64_oracle_coeffs.npz: the run with every coefficient of the tables
 multiplied by 1 + 4.4e-16 * N(0, 1) (seed 12347), i.e. changed by about two
 ulps, the size of the differences between two correct FP64 evaluations of the
 coefficient formulas (their transcendental functions are not correctly
-rounded); stored on every 8th theta row and 16th r* column.
+rounded); stored on every 8th theta row and 16th r* column.  With --extcoeffs
+it writes kerr_25601x64_oracle_extcoeffs.npz: the run from coefficient tables
+evaluated in extended precision and rounded to FP64 once
+(oracle.coeffs_ext.tables), which differ from the FP64 tables where the
+coefficient formulas cancel (c1R near the horizon keeps two or three digits in
+FP64); stored like the --coeffs run.
 
 With --perturbed it writes kerr_25601x64_oracle_perturbed.npz instead: the same
 run from the real initial plane times 1 + 2.2e-16 * N(0, 1) (numpy's default
@@ -27,7 +32,7 @@ differences two correct implementations accumulate.  The differences of these
 runs from the plain one are the run's own conditioning, which sets the parity
 bar of the full-length test.
 
-    python tests/golden/make_kerr_golden.py [threads] [--perturbed | --noisy | --fma | --coeffs]
+    python tests/golden/make_kerr_golden.py [threads] [--perturbed | --noisy | --fma | --coeffs | --extcoeffs]
 """
 import math
 import os
@@ -62,8 +67,10 @@ def main():
     noisy = "--noisy" in sys.argv
     fma = "--fma" in sys.argv
     coeffs = "--coeffs" in sys.argv
-    assert perturbed + noisy + fma + coeffs <= 1, "one variant at a time"
-    rows, cols = (SPARSE_ROWS, SPARSE_COLS) if (perturbed or noisy or coeffs) else (ROWS, COLS)
+    extcoeffs = "--extcoeffs" in sys.argv
+    assert perturbed + noisy + fma + coeffs + extcoeffs <= 1, "one variant at a time"
+    sparse = perturbed or noisy or coeffs or extcoeffs
+    rows, cols = (SPARSE_ROWS, SPARSE_COLS) if sparse else (ROWS, COLS)
     if args:
         oracle.set_threads(int(args[0]))
     w = KERR_25601x64
@@ -76,6 +83,10 @@ def main():
         crng = np.random.default_rng(SEED + 2)
         sol.replace_coeffs(node * (1.0 + COEF_EPS * crng.standard_normal(node.shape)),
                            half * (1.0 + COEF_EPS * crng.standard_normal(half.shape)))
+    if extcoeffs:
+        from oracle import coeffs_ext
+        sol.replace_coeffs(*coeffs_ext.tables(w.M, w.a, w.s, w.m, w.variable, w.rs_min, sol.drs,
+                                              w.Nr, w.Ntheta))
     re, im = initial_planes(w)
     if perturbed:
         re = re * (1.0 + EPS * np.random.default_rng(SEED).standard_normal(re.shape))
@@ -100,7 +111,7 @@ def main():
     np.savez_compressed(
         os.path.join(HERE, "kerr_25601x64_oracle" + ("_perturbed" if perturbed else "")
                      + ("_noisy" if noisy else "") + ("_fma" if fma else "")
-                     + ("_coeffs" if coeffs else "") + ".npz"),
+                     + ("_coeffs" if coeffs else "") + ("_extcoeffs" if extcoeffs else "") + ".npz"),
         wave0=sol.waveform(ids[0]), wave1=sol.waveform(ids[1]),
         state_sub=phys[:, rows, cols], plane_norms=np.linalg.norm(phys.reshape(4, -1), axis=1),
         rows=np.arange(w.Ntheta)[rows], cols=np.arange(w.Nr)[cols],
@@ -109,7 +120,8 @@ def main():
                       + (f", state times 1 + {NOISE_EPS} N(0,1) every {NOISE_EVERY} outer steps, seed "
                          f"{SEED + 1}" if noisy else "")
                       + (", oracle compiled with FMA contraction" if fma else "")
-                      + (f", coefficients times 1 + {COEF_EPS} N(0,1), seed {SEED + 2}" if coeffs else "")))
+                      + (f", coefficients times 1 + {COEF_EPS} N(0,1), seed {SEED + 2}" if coeffs else "")
+                      + (", coefficients evaluated in extended precision" if extcoeffs else "")))
 
 
 if __name__ == "__main__":
