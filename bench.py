@@ -656,14 +656,19 @@ def measure_solve(args, tk, torch, w, precision, steps, warmup, rank, world, loc
     # the library's default: FP32 runs the solve's inner steps as sweeps of
     # four in one persistent launch (whole outer steps), the rest as pairs in
     # a second one and an odd last step alone; FP64 launches one step at a
-    # time on this grid
+    # time, or all of them in one persistent launch on small grids
     spl = FP32_STEPS_PER_SWEEP if precision == 1 else 1
     inner_steps = n_outer * w.substeps
+    # FP64 on grids too small for one block per SM: every step of the solve
+    # in one persistent launch (the library's choice, read back)
+    fp64_persistent = precision == 0 and tk.tk_get_steps_per_launch(solver.h) == -1
     if precision == 1:
         unit = w.substeps // math.gcd(spl, w.substeps)
         sweeps = inner_steps // spl // unit * unit
         rest = inner_steps - sweeps * spl
         step_launches = int(sweeps > 0) + int(rest >= 2) + rest % 2
+    elif fp64_persistent:
+        step_launches = 1
     else:
         step_launches = inner_steps
     launches_per_solve = 3 + step_launches + len(w.observers)
@@ -729,7 +734,8 @@ def measure_solve(args, tk, torch, w, precision, steps, warmup, rank, world, loc
         peak = NUM_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * f_clk / 1e12
         probe = fp64_probe(tk, f_clk)
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "lw_step_kernel<double>",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "lw_persistent_kernel<double>" if fp64_persistent else "lw_step_kernel<double>",
                 "peak_source": "152 SMs x 2 DFMA/clk x 2 flop x median SM clock "
                                f"{f_clk / 1e6:.0f} MHz (GB300 FP64 FMA issue rate; "
                                "profiles/fp64_pipe_peak.md)",
@@ -739,7 +745,8 @@ def measure_solve(args, tk, torch, w, precision, steps, warmup, rank, world, loc
                 "traffic_source": traffic_src, "flop_per_update": FP64_FLOP_PER_UPDATE,
                 "fp64_issue_frac": FP64_INSTR_PER_UPDATE * pts / kern_s /
                 (NUM_SMS * FP64_FMA_PER_CLK_PER_SM * f_clk),
-                "launch_us": kern_s * 1e6}
+                "step_us": kern_s * 1e6,
+                "launch_us": kern_s * 1e6 * (inner_steps if fp64_persistent else 1)}
     else:
         # the unit of work is one sweep of FP32_STEPS_PER_SWEEP inner steps: it
         # reads u^n and the compact tables once and writes u^{n+4}; algorithmic

@@ -300,6 +300,11 @@ tk_status tk_stability_bound(tk_solver *S, double growth_per_step, double *dt_ma
  * other values. */
 tk_status tk_set_steps_per_launch(tk_solver *S, int steps);
 
+/* The launch structure tk_step uses now: -1, 1 or 2 as in
+ * tk_set_steps_per_launch, with the default (0) resolved to the choice it
+ * made for this grid and precision.  The paper has no counterpart. */
+tk_status tk_get_steps_per_launch(const tk_solver *S, int *steps);
+
 /* Lax-Wendroff steps per outer step in use (the count chosen at the last
  * tk_precompute_coeffs when the grid was made with substeps = 0). */
 tk_status tk_get_substeps(const tk_solver *S, int *substeps);

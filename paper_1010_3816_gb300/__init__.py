@@ -34,7 +34,7 @@ EXPORTS = ("tk_make_grid", "tk_precompute_coeffs", "tk_set_initial_data", "tk_ad
            "tk_extract_noalloc", "tk_adjoint", "tk_set_initial_gaussian", "tk_get_substeps",
            "tk_set_steps_per_launch", "tk_param_gradient", "tk_check_bounded_wait",
            "tk_inject_wait_timeout", "tk_probe_fp64_fma", "tk_set_coefficients",
-           "tk_get_coefficients")
+           "tk_get_coefficients", "tk_get_steps_per_launch")
 
 
 class TkError(RuntimeError):
@@ -88,6 +88,7 @@ def load_library(path: str = LIB_PATH):
             "tk_set_initial_gaussian": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double,
                                                   C.c_double, C.c_uint64]),
             "tk_get_substeps": (C.c_int, [_vp, _ip]),
+            "tk_get_steps_per_launch": (C.c_int, [_vp, _ip]),
             "tk_set_steps_per_launch": (C.c_int, [_vp, C.c_int]),
             "tk_param_gradient": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_int,
                                             C.POINTER(C.c_double)]),
@@ -312,6 +313,13 @@ def tk_get_substeps(h) -> int:
 
 def tk_set_steps_per_launch(h, steps: int) -> None:
     _check(h, load_library().tk_set_steps_per_launch(h, int(steps)))
+
+
+def tk_get_steps_per_launch(h) -> int:
+    """-1 (persistent), 1 or 2: the launch structure tk_step uses now."""
+    v = C.c_int(0)
+    _check(h, load_library().tk_get_steps_per_launch(h, C.byref(v)))
+    return v.value
 
 
 def tk_set_graph_chunk(h, outer_steps: int) -> None:

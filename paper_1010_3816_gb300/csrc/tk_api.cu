@@ -407,6 +407,13 @@ tk_status tk_get_substeps(const tk_solver *S, int *substeps)
     return TK_OK;
 }
 
+tk_status tk_get_steps_per_launch(const tk_solver *S, int *steps)
+{
+    if (!S || !steps) return fail(nullptr, TK_ERR_ARG, "tk_get_steps_per_launch: NULL argument");
+    *steps = S->persist ? -1 : (S->fuse ? 2 : 1);
+    return TK_OK;
+}
+
 static tk_status import_planes(tk_solver *S, const double *pr, const double *pi, const double *qr,
                                const double *qi, int on_device)
 {
