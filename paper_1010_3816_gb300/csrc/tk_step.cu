@@ -210,12 +210,15 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
 // Many Lax-Wendroff steps in one launch, for grids too small to fill the GPU
 // with long sweeps, where per-launch overhead would dominate.  All blocks are
 // resident at once (cooperative launch).  After each step a block publishes
-// the step count in flags[block]; in the next step it waits until both
-// neighbouring blocks have published it before it touches the columns that
-// involve them (it reads one column of u from each, and overwrites the level
-// they read in the step before; step_sweep_split).  Every wait is bounded:
-// after kMaxSpins polls the block sets *err and every block leaves its loop
-// (the state is then invalid and the host reports the error).  State loads go
+// the step count in flags[block]; in the next step the warp holding its first
+// (last) column waits until the left (right) neighbouring block has published
+// it before it touches that column (it reads one column of u from the
+// neighbour, and overwrites the level the neighbour read in the step before;
+// step_sweep_split).  Every wait is bounded: after kMaxSpins polls the warp
+// sets *err, and from then on every wait returns at once, so this kernel runs
+// its remaining steps without waiting and the persistent kernels below leave
+// their loops (the state is then invalid and the host reports the error).
+// State loads go
 // through L2 (other blocks write them).  u0 holds u^n at the start; the result
 // is in u0 or u1 by the parity of n_inner.
 constexpr long long kMaxSpins = 1ll << 24;
@@ -257,8 +260,9 @@ __device__ __forceinline__ bool neighbour_barrier(unsigned int *flags, unsigned 
 
 // Split form of the neighbour barrier for the persistent one-step sweep: a
 // block publishes that its previous step is complete, forms the part of the
-// next step that needs nothing from its neighbours, and only then waits for
-// them (bounded, as neighbour_barrier).
+// next step that needs nothing from its neighbours, and only then do the two
+// warps whose columns involve a neighbour wait for it (bounded, as
+// neighbour_barrier).
 __device__ __forceinline__ void publish_epoch(unsigned int *flags, unsigned int epoch)
 {
     __syncthreads();                       // the block's stores of the last step are issued
@@ -268,42 +272,35 @@ __device__ __forceinline__ void publish_epoch(unsigned int *flags, unsigned int 
     }
 }
 
-__device__ __forceinline__ bool wait_neighbours(unsigned int *flags, unsigned int epoch, int *err)
+// A whole warp waits (bounded) until *flag >= epoch; every lane reads the
+// flag with acquire semantics, and the lanes leave together.
+__device__ __forceinline__ void warp_wait_flag(const unsigned int *flag, unsigned int epoch, int *err)
 {
-    __shared__ int ok;
-    if (threadIdx.x == 0) {
-        int good = 1;
-        for (int side = -1; side <= 1 && good; side += 2) {
-            const int nb = (int)blockIdx.x + side;
-            if (nb < 0 || nb >= (int)gridDim.x) continue;
-            long long spins = 0;
-            while (load_acquire(&flags[nb]) < epoch) {
-                if (++spins > kMaxSpins || *(volatile int *)err) {
-                    good = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
+    long long spins = 0;
+    while (!__all_sync(0xffffffffu, load_acquire(flag) >= epoch)) {
+        if (__any_sync(0xffffffffu, ++spins > kMaxSpins || *(volatile int *)err != 0)) {
+            if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
+            return;
         }
-        if (!good) atomicExch(err, 1);
-        ok = good;
+        __nanosleep(64);
     }
-    __syncthreads();
-    return ok != 0;
 }
 
-// One step of the persistent sweep in two phases around the wait for the
-// neighbouring blocks.  Before it: every node and half node that reads and
+// One step of the persistent sweep in two phases around the waits for the
+// neighbouring blocks.  Before them: every node and half node that reads and
 // writes only this block's columns (u^n of the block's columns was written by
-// this block in the previous step).  After it: the block's first column (its
-// left half node reads the left neighbour's last column) and its last column
-// (its right half node reads the right neighbour's first column), which are
-// also the only columns of u^n the neighbours read, so they are overwritten
-// only once the neighbours have finished their previous step; and the first
-// node of every warp, deferred as in step_sweep.  Same arithmetic on the same
-// operands as step_sweep.
+// this block in the previous step).  After them: the block's first column (its
+// left half node reads the left neighbour's last column; the warp holding it
+// waits for the left neighbour) and its last column (its right half node reads
+// the right neighbour's first column; that warp waits for the right
+// neighbour), which are also the only columns of u^n the neighbours read, so
+// they are overwritten only once the neighbour concerned has finished its
+// previous step; and the first node of every warp, deferred as in step_sweep.
+// After a wait ran out every later wait returns at once (the error flag is
+// set), so the launch still ends; its result is then discarded by the host.
+// Same arithmetic on the same operands as step_sweep.
 template <typename T, int K, int W>
-__device__ __forceinline__ bool step_sweep_split(unsigned char *sh_raw, const T *__restrict__ u_in,
+__device__ __forceinline__ void step_sweep_split(unsigned char *sh_raw, const T *__restrict__ u_in,
                                                  T *__restrict__ u_out, const T *__restrict__ half,
                                                  const T *__restrict__ node, int Nr, T en,
                                                  const WaveArgs &wa, int write, int sample_offset,
@@ -363,10 +360,10 @@ __device__ __forceinline__ bool step_sweep_split(unsigned char *sh_raw, const T 
 #pragma unroll
                 for (int t = 0; t < K; ++t) sh[wib][0][c][row + t] = hm[c][t];
     }
+    __syncthreads();   // the warps' phase-1 stashes are visible
     if (epoch > 0) {
-        if (!wait_neighbours(flags, epoch, err)) return false;
-    } else {
-        __syncthreads();
+        if (lead && blockIdx.x > 0) warp_wait_flag(flags + blockIdx.x - 1, epoch, err);
+        if (last && blockIdx.x + 1 < gridDim.x) warp_wait_flag(flags + blockIdx.x + 1, epoch, err);
     }
     if (last) {
         const int i = i1 - 1;
@@ -422,7 +419,6 @@ __device__ __forceinline__ bool step_sweep_split(unsigned char *sh_raw, const T 
         store_col<T, K>(u_out + (size_t)i0 * SP + row, o);
         if (write) observe<T, K>(i0, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, sample_offset);
     }
-    return true;
 }
 
 template <typename T, int K, int W>
@@ -436,9 +432,8 @@ lw_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__restri
         T *out = (s & 1) ? u0 : u1;
         const int write = wa.write && ((s + 1) % substeps == 0);
         if (s > 0) publish_epoch(flags, (unsigned)s);
-        if (!step_sweep_split<T, K, W>(sh_raw, in, out, half, node, Nr, en, wa, write, (s + 1) / substeps - 1,
-                                       flags, (unsigned)s, err))
-            break;
+        step_sweep_split<T, K, W>(sh_raw, in, out, half, node, Nr, en, wa, write, (s + 1) / substeps - 1,
+                                  flags, (unsigned)s, err);
     }
     if (wa.write) advance_sample(wa, n_inner / substeps);
 }
