@@ -293,10 +293,10 @@ tk_status tk_stability_bound(tk_solver *S, double growth_per_step, double *dt_ma
  * pairs of inner steps run in one launch that reads the state and the
  * coefficient tables once; each warp recomputes the intermediate level one
  * column beyond its range, which adds arithmetic but no DRAM traffic.  With
- * -1, all blocks stay resident (cooperative launch) and each waits after
- * every step for its two neighbouring blocks; the waits are bounded, and
- * tk_step then synchronizes the stream and returns TK_ERR_INTERNAL if one
- * ran out.  Results are bit-identical in every mode.  Returns TK_ERR_ARG for
+ * -1, all blocks stay resident (cooperative launch) and a block waits for
+ * its two neighbouring blocks' previous step (or sweep) only where its
+ * columns involve theirs; the waits are bounded, and tk_step then
+ * synchronizes the stream and returns TK_ERR_INTERNAL if one ran out.  Results are bit-identical in every mode.  Returns TK_ERR_ARG for
  * other values. */
 tk_status tk_set_steps_per_launch(tk_solver *S, int steps);
 
