@@ -365,13 +365,15 @@ void tk_batch_destroy(tk_batch *B);
 /* Diagnostic of the bounded waits of the persistent launches (tk_step with
  * tk_set_steps_per_launch -1): a cooperative launch of n_blocks (2..64)
  * one-warp blocks, each publishing a flag and then waiting, at most max_polls
- * polls, for its two neighbours' flags, as the persistent kernels do between
- * steps -- except block `silent` (-1: none), which never publishes.  The
- * waits of its neighbours run out, set the launch's error flag, and every
- * block returns; the context stays usable.  *timed_out = 1 if the error flag
- * was set (where tk_step reports TK_ERR_INTERNAL).  The persistent kernels use
- * 2^24 polls.  Runs on the legacy default stream and synchronizes.
- * TK_ERR_ARG for arguments out of range (message in tk_last_error(NULL)). */
+ * polls each time, for its two neighbours' flags, first as the persistent
+ * kernels' blocks do between steps and then as the one-step sweep's edge
+ * warps do -- except block `silent` (-1: none), which never publishes.  Both
+ * waits of its neighbours run out, each sets its own error flag, and every
+ * block returns; the context stays usable.  *timed_out = 1 if both error
+ * flags were set (where tk_step reports TK_ERR_INTERNAL), 0 if neither was;
+ * TK_ERR_INTERNAL if only one was.  The persistent kernels use 2^24 polls.
+ * Runs on the legacy default stream and synchronizes.  TK_ERR_ARG for
+ * arguments out of range (message in tk_last_error(NULL)). */
 tk_status tk_check_bounded_wait(int n_blocks, int silent, int64_t max_polls, int *timed_out);
 
 /* Measured rate of this GPU's FP64 fused multiply-add pipe (not in the

@@ -904,19 +904,24 @@ tk_status tk_check_bounded_wait(int n_blocks, int silent, int64_t max_polls, int
         return TK_ERR_ARG;
     }
     unsigned int *flags = nullptr;
-    const size_t bytes = (size_t)n_blocks * sizeof(unsigned int) + sizeof(int);
+    const size_t bytes = (size_t)n_blocks * sizeof(unsigned int) + 2 * sizeof(int);
     cudaError_t e = cudaMalloc((void **)&flags, bytes);
     if (e == cudaSuccess) e = cudaMemset(flags, 0, bytes);
-    int *err = (int *)(flags + n_blocks);
+    int *err = (int *)(flags + n_blocks);   // [0] block-level wait, [1] warp-level wait
     if (e == cudaSuccess) e = tk::launch_wait_check(n_blocks, silent, (long long)max_polls, flags, err, 0);
-    int h = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+    int h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpy(h, err, sizeof h, cudaMemcpyDeviceToHost);
     if (flags) cudaFree(flags);
     if (e != cudaSuccess) {
         snprintf(g_err, sizeof g_err, "tk_check_bounded_wait: %s", cudaGetErrorString(e));
         return TK_ERR_CUDA;
     }
-    *timed_out = h != 0;
+    if ((h[0] != 0) != (h[1] != 0)) {
+        snprintf(g_err, sizeof g_err, "tk_check_bounded_wait: only the %s wait ran out",
+                 h[0] ? "block-level" : "warp-level");
+        return TK_ERR_INTERNAL;
+    }
+    *timed_out = h[0] != 0;
     return TK_OK;
 }
 

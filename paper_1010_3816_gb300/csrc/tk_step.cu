@@ -274,11 +274,12 @@ __device__ __forceinline__ void publish_epoch(unsigned int *flags, unsigned int 
 
 // A whole warp waits (bounded) until *flag >= epoch; every lane reads the
 // flag with acquire semantics, and the lanes leave together.
-__device__ __forceinline__ void warp_wait_flag(const unsigned int *flag, unsigned int epoch, int *err)
+__device__ __forceinline__ void warp_wait_flag(const unsigned int *flag, unsigned int epoch, int *err,
+                                               long long max_spins = kMaxSpins)
 {
     long long spins = 0;
     while (!__all_sync(0xffffffffu, load_acquire(flag) >= epoch)) {
-        if (__any_sync(0xffffffffu, ++spins > kMaxSpins || *(volatile int *)err != 0)) {
+        if (__any_sync(0xffffffffu, ++spins > max_spins || *(volatile int *)err != 0)) {
             if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
             return;
         }
@@ -438,14 +439,18 @@ lw_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__restri
     if (wa.write) advance_sample(wa, n_inner / substeps);
 }
 
-// Diagnostic of the bounded wait: every block but `silent` publishes epoch 1
-// and waits for its neighbours as the persistent kernels do between steps;
-// `silent` returns at once, so its neighbours' waits run out after max_spins
-// polls and set *err.
+// Diagnostic of the bounded waits: every block but `silent` publishes epoch 1
+// and waits for its neighbours as the persistent kernels do between steps
+// (the block-level wait, error word err[0]), then waits for each neighbour
+// as the edge warps of the one-step sweep do (the warp-level wait, err[1]);
+// `silent` returns at once, so both waits of its neighbours run out after
+// max_spins polls and set their error words.
 __global__ void wait_check_kernel(unsigned int *flags, int *err, int silent, long long max_spins)
 {
     if ((int)blockIdx.x == silent) return;
     neighbour_barrier(flags, 1u, err, max_spins);
+    if (blockIdx.x > 0) warp_wait_flag(flags + blockIdx.x - 1, 1u, err + 1, max_spins);
+    if (blockIdx.x + 1 < gridDim.x) warp_wait_flag(flags + blockIdx.x + 1, 1u, err + 1, max_spins);
 }
 
 // Two Lax-Wendroff steps per launch, u^n -> u^{n+2}, for the HBM-bound
