@@ -367,11 +367,12 @@ void tk_batch_destroy(tk_batch *B);
  * one-warp blocks, each publishing a flag and then waiting, at most max_polls
  * polls each time, for its two neighbours' flags, first as the persistent
  * kernels' blocks do between steps and then as the one-step sweep's edge
- * warps do -- except block `silent` (-1: none), which never publishes.  Both
- * waits of its neighbours run out, each sets its own error flag, and every
- * block returns; the context stays usable.  *timed_out = 1 if both error
- * flags were set (where tk_step reports TK_ERR_INTERNAL), 0 if neither was;
- * TK_ERR_INTERNAL if only one was.  The persistent kernels use 2^24 polls.
+ * warps do -- except block `silent` (-1: none), which never publishes and
+ * instead waits on a shared-memory counter that nothing sets, as the one-step
+ * sweep's warps wait for their siblings.  All three kinds of wait run out,
+ * each sets its own error flag, and every block returns; the context stays
+ * usable.  *timed_out = 1 if all three error flags were set (where tk_step
+ * reports TK_ERR_INTERNAL), 0 if none was; TK_ERR_INTERNAL if only some were.  The persistent kernels use 2^24 polls.
  * Runs on the legacy default stream and synchronizes.  TK_ERR_ARG for
  * arguments out of range (message in tk_last_error(NULL)). */
 tk_status tk_check_bounded_wait(int n_blocks, int silent, int64_t max_polls, int *timed_out);

@@ -620,7 +620,8 @@ tk_status tk_step(tk_solver *S, int n)
     if (S->persist && (long long)n * S->substeps >= 2) {
         // every inner step of the call in one cooperative launch; its waits
         // are bounded, and a wait that timed out is reported here
-        const int nflags = S->persist_blocks > S->multi_blocks ? S->persist_blocks : S->multi_blocks;
+        // the one-step sweep keeps two flags per block (its first and last warp)
+        const int nflags = 2 * S->persist_blocks > S->multi_blocks ? 2 * S->persist_blocks : S->multi_blocks;
         const size_t fbytes = (size_t)nflags * sizeof(unsigned int) + sizeof(int);
         if (!S->pflags) {
             st = alloc(S, (void **)&S->pflags, fbytes);
@@ -904,24 +905,27 @@ tk_status tk_check_bounded_wait(int n_blocks, int silent, int64_t max_polls, int
         return TK_ERR_ARG;
     }
     unsigned int *flags = nullptr;
-    const size_t bytes = (size_t)n_blocks * sizeof(unsigned int) + 2 * sizeof(int);
+    const size_t bytes = (size_t)n_blocks * sizeof(unsigned int) + 3 * sizeof(int);
     cudaError_t e = cudaMalloc((void **)&flags, bytes);
     if (e == cudaSuccess) e = cudaMemset(flags, 0, bytes);
-    int *err = (int *)(flags + n_blocks);   // [0] block-level wait, [1] warp-level wait
+    // [0] the blocks' neighbour barrier, [1] a warp on a global flag, [2] a
+    // warp on a shared-memory counter
+    int *err = (int *)(flags + n_blocks);
     if (e == cudaSuccess) e = tk::launch_wait_check(n_blocks, silent, (long long)max_polls, flags, err, 0);
-    int h[2] = {0, 0};
+    int h[3] = {0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpy(h, err, sizeof h, cudaMemcpyDeviceToHost);
     if (flags) cudaFree(flags);
     if (e != cudaSuccess) {
         snprintf(g_err, sizeof g_err, "tk_check_bounded_wait: %s", cudaGetErrorString(e));
         return TK_ERR_CUDA;
     }
-    if ((h[0] != 0) != (h[1] != 0)) {
-        snprintf(g_err, sizeof g_err, "tk_check_bounded_wait: only the %s wait ran out",
-                 h[0] ? "block-level" : "warp-level");
+    const int n_out = (h[0] != 0) + (h[1] != 0) + (h[2] != 0);
+    if (n_out != 0 && n_out != 3) {
+        snprintf(g_err, sizeof g_err, "tk_check_bounded_wait: only some waits ran out (%d %d %d)", h[0] != 0,
+                 h[1] != 0, h[2] != 0);
         return TK_ERR_INTERNAL;
     }
-    *timed_out = h[0] != 0;
+    *timed_out = n_out == 3;
     return TK_OK;
 }
 

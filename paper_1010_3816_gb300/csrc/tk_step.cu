@@ -209,12 +209,11 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
 
 // Many Lax-Wendroff steps in one launch, for grids too small to fill the GPU
 // with long sweeps, where per-launch overhead would dominate.  All blocks are
-// resident at once (cooperative launch).  After each step a block publishes
-// the step count in flags[block]; in the next step the warp holding its first
-// (last) column waits until the left (right) neighbouring block has published
-// it before it touches that column (it reads one column of u from the
-// neighbour, and overwrites the level the neighbour read in the step before;
-// step_sweep_split).  Every wait is bounded: after kMaxSpins polls the warp
+// resident at once (cooperative launch).  There is no barrier between steps:
+// each warp waits only for the warps whose data it reads or overwrites -- its
+// two siblings in the block, and for a block's first and last warp the edge
+// warp of the neighbouring block -- through counters of finished steps
+// (step_sweep_async).  Every wait is bounded: after kMaxSpins polls the warp
 // sets *err, and from then on every wait returns at once, so this kernel runs
 // its remaining steps without waiting and the persistent kernels below leave
 // their loops (the state is then invalid and the host reports the error).
@@ -258,20 +257,6 @@ __device__ __forceinline__ bool neighbour_barrier(unsigned int *flags, unsigned 
     return ok != 0;
 }
 
-// Split form of the neighbour barrier for the persistent one-step sweep: a
-// block publishes that its previous step is complete, forms the part of the
-// next step that needs nothing from its neighbours, and only then do the two
-// warps whose columns involve a neighbour wait for it (bounded, as
-// neighbour_barrier).
-__device__ __forceinline__ void publish_epoch(unsigned int *flags, unsigned int epoch)
-{
-    __syncthreads();                       // the block's stores of the last step are issued
-    if (threadIdx.x == 0) {
-        __threadfence();                   // and visible to the other blocks
-        atomicExch(&flags[blockIdx.x], epoch);
-    }
-}
-
 // A whole warp waits (bounded) until *flag >= epoch; every lane reads the
 // flag with acquire semantics, and the lanes leave together.
 __device__ __forceinline__ void warp_wait_flag(const unsigned int *flag, unsigned int epoch, int *err,
@@ -287,25 +272,84 @@ __device__ __forceinline__ void warp_wait_flag(const unsigned int *flag, unsigne
     }
 }
 
-// One step of the persistent sweep in two phases around the waits for the
-// neighbouring blocks.  Before them: every node and half node that reads and
-// writes only this block's columns (u^n of the block's columns was written by
-// this block in the previous step).  After them: the block's first column (its
-// left half node reads the left neighbour's last column; the warp holding it
-// waits for the left neighbour) and its last column (its right half node reads
-// the right neighbour's first column; that warp waits for the right
-// neighbour), which are also the only columns of u^n the neighbours read, so
-// they are overwritten only once the neighbour concerned has finished its
-// previous step; and the first node of every warp, deferred as in step_sweep.
-// After a wait ran out every later wait returns at once (the error flag is
-// set), so the launch still ends; its result is then discarded by the host.
+// Progress counters between the warps of a block, in shared memory: a
+// release store after the warp's writes, acquire loads by the waiting warp.
+__device__ __forceinline__ void cta_release(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)),
+                 "r"(v)
+                 : "memory");
+}
+
+__device__ __forceinline__ unsigned int cta_acquire(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];"
+                 : "=r"(v)
+                 : "r"((unsigned)__cvta_generic_to_shared(p))
+                 : "memory");
+    return v;
+}
+
+// A whole warp waits (bounded) until the shared counter *c >= v.
+__device__ __forceinline__ void warp_wait_cta(const unsigned int *c, unsigned int v, int *err,
+                                              long long max_spins = kMaxSpins)
+{
+    long long spins = 0;
+    while (!__all_sync(0xffffffffu, cta_acquire(c) >= v)) {
+        if (__any_sync(0xffffffffu, ++spins > max_spins || *(volatile int *)err != 0)) {
+            if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
+            return;
+        }
+        __nanosleep(32);
+    }
+}
+
+// The warp's writes so far are visible to the block (cta) or to the GPU
+// before the counter or flag says so.
+__device__ __forceinline__ void warp_publish_cta(unsigned int *c, unsigned int v)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) cta_release(c, v);
+}
+
+__device__ __forceinline__ void warp_publish_gpu(unsigned int *f, unsigned int v)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence();
+        atomicExch(f, v);
+    }
+}
+
+// One step of the persistent sweep with no block barrier: every warp waits
+// only for what it uses.  Counters (number of finished steps, or of steps
+// whose first phase is finished) per warp in shared memory, and per block
+// for its first and last warp in global memory (flags[b] and
+// flags[blocks + b]).  Step s of warp w:
+//   - first phase (every half node and node that involves only the block's
+//     columns, as in step_sweep): it reads the right sibling's first column
+//     and overwrites its own last half node, which the right sibling read in
+//     the last step, so it waits until that sibling has finished step s - 1;
+//     then it publishes that its first phase of step s is done;
+//   - the block's last warp waits until the right neighbouring block's first
+//     warp has finished step s - 1 (it reads that warp's column, and
+//     overwrites its own last column, which that warp read), then forms it;
+//   - the deferred first node: the block's first warp waits until the left
+//     neighbouring block's last warp has finished step s - 1 and forms its
+//     left half node from that warp's column; every other warp waits until
+//     its left sibling's first phase of step s is done and takes that
+//     sibling's last half node;
+//   - it publishes that it has finished step s.
+// Every wait is bounded; after one ran out every later wait returns at once.
 // Same arithmetic on the same operands as step_sweep.
 template <typename T, int K, int W>
-__device__ __forceinline__ void step_sweep_split(unsigned char *sh_raw, const T *__restrict__ u_in,
+__device__ __forceinline__ void step_sweep_async(unsigned char *sh_raw, const T *__restrict__ u_in,
                                                  T *__restrict__ u_out, const T *__restrict__ half,
                                                  const T *__restrict__ node, int Nr, T en,
                                                  const WaveArgs &wa, int write, int sample_offset,
-                                                 unsigned int *flags, unsigned int epoch, int *err)
+                                                 unsigned int *flags, unsigned int *first_done,
+                                                 unsigned int *step_done, unsigned int s, int *err)
 {
     constexpr int NP = 32 * K;
     constexpr size_t SP = 4 * NP, HP = (size_t)kNCH * NP, NQ = (size_t)kNCN * NP;
@@ -314,59 +358,56 @@ __device__ __forceinline__ void step_sweep_split(unsigned char *sh_raw, const T 
     const int wib = threadIdx.x >> 5;
     int i0, i1, left;
     warp_range<W>(Nr, wib, &i0, &i1, &left);
+    if (i1 <= i0) return;   // (every warp has a column on the grids this kernel runs)
     const int row = lane * K;
     const bool lead = (left < 0);
     const int b1 = (int)(((long long)(blockIdx.x + 1) * Nr) / gridDim.x);
-    const bool last = (i1 > i0) && (i1 == b1);
+    const bool last = (i1 == b1);
     const int iend = last ? i1 - 1 : i1;
+    const unsigned int nb = gridDim.x;
+    if (s > 0 && !last) warp_wait_cta(&step_done[wib + 1], s, err);
     T ua[4][K], hm[4][K];
     zero_col<T, K>(hm);
-    if (i1 > i0) {
-        load_state<T, K, true>(u_in + (size_t)i0 * SP + row, ua);
-        for (int i = i0; i < iend; ++i) {
-            T uc[4][K], hp[4][K], o[4][K];
-            if (i + 1 < Nr) {
-                load_state<T, K, true>(u_in + (size_t)(i + 1) * SP + row, uc);
-                half_node<T, K>(ua, uc, half + (size_t)i * HP + row, hp);
-            } else {
-                zero_col<T, K>(uc);
-                zero_col<T, K>(hp);
-            }
-            if (i == i0) {
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-#pragma unroll
-                    for (int t = 0; t < K; ++t) {
-                        sh[wib][1][c][row + t] = ua[c][t];
-                        sh[wib][2][c][row + t] = hp[c][t];
-                    }
-            } else {
-                full_node<T, K>(hm, hp, ua, node + (size_t)i * NQ + row, en, o);
-                if (i == 0 || i == Nr - 1) zero_col<T, K>(o);
-                store_col<T, K>(u_out + (size_t)i * SP + row, o);
-                if (write)
-                    observe<T, K>(i, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, sample_offset);
-            }
+    load_state<T, K, true>(u_in + (size_t)i0 * SP + row, ua);
+    for (int i = i0; i < iend; ++i) {
+        T uc[4][K], hp[4][K], o[4][K];
+        if (i + 1 < Nr) {
+            load_state<T, K, true>(u_in + (size_t)(i + 1) * SP + row, uc);
+            half_node<T, K>(ua, uc, half + (size_t)i * HP + row, hp);
+        } else {
+            zero_col<T, K>(uc);
+            zero_col<T, K>(hp);
+        }
+        if (i == i0) {
 #pragma unroll
             for (int c = 0; c < 4; ++c)
 #pragma unroll
                 for (int t = 0; t < K; ++t) {
-                    hm[c][t] = hp[c][t];
-                    ua[c][t] = uc[c][t];
+                    sh[wib][1][c][row + t] = ua[c][t];
+                    sh[wib][2][c][row + t] = hp[c][t];
                 }
+        } else {
+            full_node<T, K>(hm, hp, ua, node + (size_t)i * NQ + row, en, o);
+            if (i == 0 || i == Nr - 1) zero_col<T, K>(o);
+            store_col<T, K>(u_out + (size_t)i * SP + row, o);
+            if (write) observe<T, K>(i, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, sample_offset);
         }
-        if (!last)   // u^{n+1/2} at i1 - 1/2: the right neighbour warp's left half node
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
+        for (int c = 0; c < 4; ++c)
 #pragma unroll
-                for (int t = 0; t < K; ++t) sh[wib][0][c][row + t] = hm[c][t];
+            for (int t = 0; t < K; ++t) {
+                hm[c][t] = hp[c][t];
+                ua[c][t] = uc[c][t];
+            }
     }
-    __syncthreads();   // the warps' phase-1 stashes are visible
-    if (epoch > 0) {
-        if (lead && blockIdx.x > 0) warp_wait_flag(flags + blockIdx.x - 1, epoch, err);
-        if (last && blockIdx.x + 1 < gridDim.x) warp_wait_flag(flags + blockIdx.x + 1, epoch, err);
-    }
+    if (!last)
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int t = 0; t < K; ++t) sh[wib][0][c][row + t] = hm[c][t];
+    warp_publish_cta(&first_done[wib], s + 1);
     if (last) {
+        if (s > 0 && blockIdx.x + 1 < nb) warp_wait_flag(flags + blockIdx.x + 1, s, err);
         const int i = i1 - 1;
         T uc[4][K], hp[4][K];
         if (i + 1 < Nr) {
@@ -391,8 +432,9 @@ __device__ __forceinline__ void step_sweep_split(unsigned char *sh_raw, const T 
             store_col<T, K>(u_out + (size_t)i * SP + row, o);
             if (write) observe<T, K>(i, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, sample_offset);
         }
+        __syncwarp();
     }
-    if (i1 > i0) {
+    {
         T hl[4][K], uf[4][K], hf[4][K], o[4][K];
 #pragma unroll
         for (int c = 0; c < 4; ++c)
@@ -402,6 +444,7 @@ __device__ __forceinline__ void step_sweep_split(unsigned char *sh_raw, const T 
                 hf[c][t] = sh[wib][2][c][row + t];
             }
         if (lead) {
+            if (s > 0 && blockIdx.x > 0) warp_wait_flag(flags + nb + blockIdx.x - 1, s, err);
             if (i0 > 0) {
                 T ul[4][K];
                 load_state<T, K, true>(u_in + (size_t)(i0 - 1) * SP + row, ul);
@@ -410,6 +453,7 @@ __device__ __forceinline__ void step_sweep_split(unsigned char *sh_raw, const T 
                 zero_col<T, K>(hl);
             }
         } else {
+            warp_wait_cta(&first_done[left], s + 1, err);
 #pragma unroll
             for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -420,6 +464,9 @@ __device__ __forceinline__ void step_sweep_split(unsigned char *sh_raw, const T 
         store_col<T, K>(u_out + (size_t)i0 * SP + row, o);
         if (write) observe<T, K>(i0, lane, o, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, sample_offset);
     }
+    if (lead) warp_publish_gpu(flags + blockIdx.x, s + 1);
+    if (last) warp_publish_gpu(flags + nb + blockIdx.x, s + 1);
+    warp_publish_cta(&step_done[wib], s + 1);
 }
 
 template <typename T, int K, int W>
@@ -428,13 +475,18 @@ lw_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__restri
                      T en, const WaveArgs wa, int n_inner, int substeps, unsigned int *flags, int *err)
 {
     extern __shared__ __align__(16) unsigned char sh_raw[];
+    __shared__ unsigned int first_done[W], step_done[W];
+    if (threadIdx.x < W) {
+        first_done[threadIdx.x] = 0;
+        step_done[threadIdx.x] = 0;
+    }
+    __syncthreads();
     for (int s = 0; s < n_inner; ++s) {
         const T *in = (s & 1) ? u1 : u0;
         T *out = (s & 1) ? u0 : u1;
         const int write = wa.write && ((s + 1) % substeps == 0);
-        if (s > 0) publish_epoch(flags, (unsigned)s);
-        step_sweep_split<T, K, W>(sh_raw, in, out, half, node, Nr, en, wa, write, (s + 1) / substeps - 1,
-                                  flags, (unsigned)s, err);
+        step_sweep_async<T, K, W>(sh_raw, in, out, half, node, Nr, en, wa, write, (s + 1) / substeps - 1, flags,
+                                  first_done, step_done, (unsigned)s, err);
     }
     if (wa.write) advance_sample(wa, n_inner / substeps);
 }
@@ -442,12 +494,20 @@ lw_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__restri
 // Diagnostic of the bounded waits: every block but `silent` publishes epoch 1
 // and waits for its neighbours as the persistent kernels do between steps
 // (the block-level wait, error word err[0]), then waits for each neighbour
-// as the edge warps of the one-step sweep do (the warp-level wait, err[1]);
-// `silent` returns at once, so both waits of its neighbours run out after
+// as the edge warps of the one-step sweep do (the warp-level wait on a global
+// flag, err[1]).  `silent` instead waits on a shared-memory counter that
+// nothing sets, as the one-step sweep's warps wait for their siblings (err[2]),
+// and returns without publishing; so all three kinds of wait run out after
 // max_spins polls and set their error words.
 __global__ void wait_check_kernel(unsigned int *flags, int *err, int silent, long long max_spins)
 {
-    if ((int)blockIdx.x == silent) return;
+    __shared__ unsigned int never;
+    if ((int)blockIdx.x == silent) {
+        if (threadIdx.x == 0) never = 0;
+        __syncwarp();
+        warp_wait_cta(&never, 1u, err + 2, max_spins);
+        return;
+    }
     neighbour_barrier(flags, 1u, err, max_spins);
     if (blockIdx.x > 0) warp_wait_flag(flags + blockIdx.x - 1, 1u, err + 1, max_spins);
     if (blockIdx.x + 1 < gridDim.x) warp_wait_flag(flags + blockIdx.x + 1, 1u, err + 1, max_spins);

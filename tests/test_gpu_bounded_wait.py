@@ -2,10 +2,11 @@
 blocks (or, in the one-step sweep, the warps at a block's two edges) wait for
 their neighbours with a bounded number of polls, after which the wait sets
 the launch's error flag and returns (tk_step then reports TK_ERR_INTERNAL).
-tk_check_bounded_wait runs both kinds of wait with one block that never
-publishes its flag: its neighbours' waits of both kinds must run out, each
-must raise its flag, every block must return, and the context must stay
-usable.  Nothing here faults, traps or hangs the GPU: every wait ends by
+tk_check_bounded_wait runs every kind of wait with one block that never
+publishes its flag and itself waits on a shared-memory counter that nothing
+sets: its neighbours' waits on the global flags and its own wait must all run
+out, each must raise its flag, every block must return, and the context must
+stay usable.  Nothing here faults, traps or hangs the GPU: every wait ends by
 itself."""
 import math
 import time
