@@ -63,15 +63,15 @@ FP64_FMA_PER_CLK_PER_SM = 2        # measured: 1.19 TFLOP/s at 1995 MHz on 152 S
 FP32_FMA_PER_CLK_PER_SM = 128
 
 
-# DRAM bytes per unit of work of the step kernel (one launch, or one sweep of
-# the FP32 persistent launch: dram__bytes_read.sum +
+# DRAM bytes per unit of work of the step kernel (one inner step of the FP64
+# persistent launch, one sweep of the FP32 one: dram__bytes_read.sum +
 # dram__bytes_write.sum from one ncu capture of the current kernel source),
 # keyed by (workload name, precision); the capture's command and figures are in the
 # named summary under profiles/.
 MEASURED_TRAFFIC = {
-    # one launch of the one-step kernel: 334.086400 + 38.545408 MB
-    ("kerr_a0.9_25601x64_38400steps", 0): (334.086400e6 + 38.545408e6,
-                                           "profiles/lw_step_f64_kerr_25601x64.md"),
+    # one persistent launch of 200 steps: 65.775047 + 10.831660 GB, per step
+    ("kerr_a0.9_25601x64_38400steps", 0): ((65.775047e9 + 10.831660e9) / 200,
+                                           "profiles/lw_persistent_f64_kerr_25601x64.md"),
     # one launch of 50 sweeps of four steps: 6.703077 + 1.271924 GB
     ("kerr_a0.9_25601x64_38400steps", 1): ((6.703077e9 + 1.271924e9) / 50,
                                            "profiles/lw_multi_persistent_f32_kerr_25601x64.md"),
@@ -655,12 +655,12 @@ def measure_solve(args, tk, torch, w, precision, steps, warmup, rank, world, loc
     updates = w.points * n_outer * w.substeps
     # the library's default: FP32 runs the solve's inner steps as sweeps of
     # four in one persistent launch (whole outer steps), the rest as pairs in
-    # a second one and an odd last step alone; FP64 launches one step at a
-    # time, or all of them in one persistent launch on small grids
+    # a second one and an odd last step alone; FP64 runs them all in one
+    # persistent launch (read back from the library)
     spl = FP32_STEPS_PER_SWEEP if precision == 1 else 1
     inner_steps = n_outer * w.substeps
-    # FP64 on grids too small for one block per SM: every step of the solve
-    # in one persistent launch (the library's choice, read back)
+    # FP64: every step of the solve in one persistent launch, unless the
+    # library chose one launch per step for this grid (read back)
     fp64_persistent = precision == 0 and tk.tk_get_steps_per_launch(solver.h) == -1
     if precision == 1:
         unit = w.substeps // math.gcd(spl, w.substeps)

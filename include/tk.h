@@ -160,11 +160,10 @@ tk_status tk_add_observer(tk_solver *S, double rstar_obs, double theta_obs, int 
 
 /* Advance n >= 0 outer steps (Eqs. lw1 then lw2, with the theta-pole ghosts
  * and radial-edge zeros folded in), appending one sample per observer per
- * outer step.  Asynchronous, except in the persistent mode of
- * tk_set_steps_per_launch (-1, the default for FP32 and for FP64 grids too
- * small for one block per SM), where every step of the call runs in one
- * cooperative launch and the call synchronizes the stream to check that
- * launch's bounded waits.  If one ran out, tk_step returns TK_ERR_INTERNAL,
+ * outer step.  In the persistent mode of tk_set_steps_per_launch (-1, the
+ * default) every step of the call runs in one cooperative launch and the call
+ * synchronizes the stream to check that launch's bounded waits; in the other
+ * modes it is asynchronous.  If one ran out, tk_step returns TK_ERR_INTERNAL,
  * the step and sample counts stay where the call found them (the samples
  * taken before it stay readable), and the state is invalid: tk_step,
  * tk_get_state, tk_check_finite, tk_adjoint and tk_param_gradient return
@@ -286,10 +285,9 @@ tk_status tk_stability_bound(tk_solver *S, double growth_per_step, double *dt_ma
  * TK_PREC_F32 sweeps of four steps over the grid where it has at least four
  * columns per warp of one block per SM -- the sweeps cover whole outer steps
  * -- and pairs of steps, in a second launch, for the rest, with an odd last
- * step launched alone), or 0 for the default: -1 for TK_PREC_F32, whose step is
- * bound by memory traffic; for TK_PREC_F64, whose step is bound by FP64
- * arithmetic, 1, or -1 on grids too small for one block per SM (where launch
- * overhead and latency dominate).  With 2,
+ * step launched alone), or 0 for the default: -1 (1 for TK_PREC_F64 and 2
+ * for TK_PREC_F32 on a grid whose blocks could not all be resident at once).
+ * With 2,
  * pairs of inner steps run in one launch that reads the state and the
  * coefficient tables once; each warp recomputes the intermediate level one
  * column beyond its range, which adds arithmetic but no DRAM traffic.  With

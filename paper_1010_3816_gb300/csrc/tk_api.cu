@@ -161,23 +161,23 @@ using tkh::need_state;
 // when the solver picks its own number of substeps: a factor e over 40000 steps.
 constexpr double kAutoGrowthPerStep = 2.5e-5;
 
-// Launch structure for tk_step.  mode 0 (automatic): FP32, bound by memory,
-// runs every step of a call in one persistent launch, as sweeps of four steps
-// on large grids and pairs of steps otherwise (four or two steps per read of
-// the state and the tables, and no per-launch tail: a block waits only for
-// its neighbours, so random differences in block speed average out); FP64, bound by its arithmetic (which the two-step kernel's
-// overlap adds to), takes one step per launch, and every step of a call in
-// one persistent launch on grids too small for one block per SM (where
-// launch overhead and latency dominate).  Measured: FP32 25601 x 64, 15.7 us
-// per step in sweeps of four, 16.6 in pairs, 18.3 with a launch per pair; FP64 1601 x 32, 9.1
-// against 9.7 us; FP64 25601 x 64, 155.3 against 155.5 us (not worth the
-// host synchronization the persistent launch needs).
+// Launch structure for tk_step.  mode 0 (automatic): every step of a call in
+// one persistent launch.  FP32, bound by memory, runs it as sweeps of four
+// steps on large grids and pairs of steps otherwise (four or two steps per
+// read of the state and the tables); FP64, bound by its arithmetic (which the
+// two-step kernel's overlap adds to), as single steps in which every warp
+// waits only for the warps it depends on, so that no launch boundary or block
+// barrier separates the steps.  Measured: FP32 25601 x 64, 15.7 us per step in
+// sweeps of four, 16.6 in pairs, 18.3 with a launch per pair; FP64 1601 x 32,
+// 6.5 against 14.5 us with a launch per step; FP64 25601 x 32 / 64 / 128, 73.3
+// / 146.9 / 287.0 against 79.0 / 150.3 / 297.4 us.  A grid whose blocks cannot
+// all be resident at once falls back to one launch per step (2 for FP32).
 static void set_launch_mode(tk_solver *S, int mode)
 {
     S->fuse_mode = mode;
     if (mode == 0) {
         if (S->precision == TK_PREC_F32) mode = S->persist_blocks > 0 ? -1 : 2;
-        else mode = (S->persist_blocks > 0 && S->warps == tk::kNarrowWarps) ? -1 : 1;
+        else mode = S->persist_blocks > 0 ? -1 : 1;
     }
     S->persist = (mode == -1);
     S->fuse = (mode == 2);

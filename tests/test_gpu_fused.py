@@ -99,11 +99,11 @@ def test_steps_per_launch_argument():
     g.close()
 
 
-@pytest.mark.parametrize("precision,Nr,want", [(0, 1601, -1), (0, 25601, 1), (1, 1601, -1), (1, 25601, -1)])
+@pytest.mark.parametrize("precision,Nr,want", [(0, 1601, -1), (0, 25601, -1), (1, 1601, -1), (1, 25601, -1)])
 def test_get_steps_per_launch_reports_the_default_choice(precision, Nr, want):
-    """The default resolved for the grid: FP64 one step per launch where the
-    grid fills one block per SM and one persistent launch below that; FP32
-    persistent everywhere.  An explicit choice reads back as set."""
+    """The default resolved for the grid: every step of a call in one
+    persistent launch, for both precisions and grid sizes.  An explicit choice
+    reads back as set."""
     import paper_1010_3816_gb300 as tk
     w = _grid(Nr, 64 if Nr > 2000 else 32)
     g = tk.Solver(rstar_min=w.rs_min, rstar_max=w.rs_max, Nr=w.Nr, Ntheta=w.Ntheta, dt=w.dt,
