@@ -358,7 +358,10 @@ __device__ __forceinline__ void step_sweep_async(unsigned char *sh_raw, const T 
     const int wib = threadIdx.x >> 5;
     int i0, i1, left;
     warp_range<W>(Nr, wib, &i0, &i1, &left);
-    if (i1 <= i0) return;   // (every warp has a column on the grids this kernel runs)
+    // The launch has at most Nr / W blocks, so every block has at least W
+    // columns and warp_range gives every warp at least one; a warp without
+    // one would never publish, and its left sibling's wait would run out.
+    if (i1 <= i0) return;
     const int row = lane * K;
     const bool lead = (left < 0);
     const int b1 = (int)(((long long)(blockIdx.x + 1) * Nr) / gridDim.x);
