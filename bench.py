@@ -370,17 +370,24 @@ def run_batched(args, tk, torch, rank, world, local, steps=None, warmup=None, em
                        "substeps_by_Ntheta": {"32": 2, "64": 4, "128": 8}, "ticks_per_outer_step": info["kmax"],
                        "segment_autotuned": seg, "tuned_ms_per_outer_step": tuned_ms,
                        "grid_blocks": info["blocks"],
+                       "strategy": ("members one after another, each as one persistent launch (the tuner's "
+                                    "choice: faster than the work queue here)") if seg == 0
+                                   else "work queue of (member, column range) items, one launch per tick",
                        "parallelism": f"instances sharded over {world} GPUs" if world > 1 else "single GPU",
                        "l2": L2_NOTE},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "batch_step_kernel<double>",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "lw_persistent_kernel<double>" if seg == 0 else "batch_step_kernel<double>",
                          "peak_source": "152 SMs x 2 DFMA/clk (measured) x 2 flop x median SM clock"},
             "plain_tk_step": {"value": plain, "unit": "updates/s",
                               "what": "the same instances through tk_step one after another"},
             "ratio_vs_sequential_tk_step": (updates / kern_s) / plain,
             "cpu_baseline": None, "e2e": None, "clocks": clk,
-            "gpu_launches": steps * (n_outer * info["kmax"] + 3 * len(inst) +
-                                          sum(len(o) for o in outs)),
+            # per timed step: the ticks (or one persistent launch per member),
+            # and per member the precompute's three launches and one read-out
+            # per observer
+            "gpu_launches": steps * ((len(inst) if seg == 0 else n_outer * info["kmax"]) + 3 * len(inst) +
+                                     sum(len(o) for o in outs)),
         }
         if emit:
             print(json.dumps(line))

@@ -341,20 +341,27 @@ tk_status tk_batch_step(tk_batch *B, int n);
 /* Autotuner (the counterpart of the paper's tuning of the work-group size,
  * Sec. 4): time trial_steps outer steps for every pair of a segment length
  * (columns per work item: 4 .. 128) and a grid size (1 .. the resident
- * maximum of blocks per SM) on the batch's own data, restore every member's
- * state and sample counter after each trial, and keep the fastest pair.
- * Writes the chosen length and its time per outer step (ms); the chosen grid
- * is reported by tk_batch_info.  Needs device memory for one copy of every
- * member's state. */
+ * maximum of blocks per SM) on the batch's own data; then, when every member
+ * fills the GPU alone (its own persistent launch has one block per SM),
+ * compare the best pair with the members stepped one after another as
+ * tk_step would step each alone, both timed on the device at trial_steps and 2 trial_steps outer
+ * steps and compared by the difference (so that fixed start-up costs count
+ * for neither); restore every member's state and sample counter after each
+ * trial, and keep the faster.  Writes the chosen segment length
+ * (0 for the members one after another) and its time per outer step (ms);
+ * the chosen grid is reported by tk_batch_info.  Results are bit-identical
+ * either way.  Needs device memory for one copy of every member's state. */
 tk_status tk_batch_tune(tk_batch *B, int trial_steps, int *best_seg, double *best_ms_per_step);
 
-/* Set the segment length directly (>= 2). */
+/* Set the segment length directly (>= 2), or 0 to step the members one after
+ * another as tk_step would (synchronizing as tk_step does). */
 tk_status tk_batch_set_segment(tk_batch *B, int seg);
 
 /* Outer steps per graph replay: -1 automatic, 0 no graph, c > 0 about c. */
 tk_status tk_batch_set_graph_chunk(tk_batch *B, int outer_steps);
 
-/* Ticks per outer step, segment length, grid size. */
+/* Ticks per outer step, segment length, grid size (segment and grid 0 when
+ * the members are stepped one after another). */
 tk_status tk_batch_info(const tk_batch *B, int *kmax, int *seg, int *blocks);
 
 const char *tk_batch_last_error(const tk_batch *B);

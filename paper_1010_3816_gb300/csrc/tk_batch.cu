@@ -170,6 +170,9 @@ struct tk_batch {
     int kmax = 1;
     int blocks = 1;
     int seg = 32;
+    // step the members one after another, each as tk_step would (segment
+    // length 0), instead of the work queue
+    bool per_member = false;
     tk::BatchMember *d_mem = nullptr;
     tk::BatchItem *d_items = nullptr;
     size_t items_cap = 0;
@@ -393,8 +396,11 @@ tk_status tk_batch_create(tk_batch **out, tk_solver *const *members, int n)
 
 tk_status tk_batch_set_segment(tk_batch *B, int seg)
 {
-    if (!B || seg < 2) return bfail(B, TK_ERR_ARG, "tk_batch_set_segment: seg must be >= 2");
+    if (!B || seg == 1 || seg < 0)
+        return bfail(B, TK_ERR_ARG, "tk_batch_set_segment: seg must be 0 or >= 2");
     TKB_CUDA(B, cudaSetDevice(B->device));
+    B->per_member = (seg == 0);
+    if (B->per_member) return TK_OK;
     return build_items(B, seg);
 }
 
@@ -412,6 +418,13 @@ tk_status tk_batch_step(tk_batch *B, int n)
     TKB_CUDA(B, cudaSetDevice(B->device));
     tk_status st = check_members(B);
     if (st != TK_OK || n == 0) return st;
+    if (B->per_member) {
+        for (tk_solver *S : B->mem) {
+            st = tk_step(S, n);
+            if (st != TK_OK) return bfail(B, st, "tk_batch_step: %s", S->err);
+        }
+        return TK_OK;
+    }
     for (tk_solver *S : B->mem) {
         st = tkh::ensure_wave(S, S->count + n);
         if (st != TK_OK) return bfail(B, st, "tk_batch_step: %s", S->err);
@@ -458,7 +471,7 @@ tk_status tk_batch_tune(tk_batch *B, int trial_steps, int *best_seg, double *bes
     tk_status st = check_members(B);
     if (st != TK_OK) return st;
     for (tk_solver *S : B->mem) {
-        st = tkh::ensure_wave(S, S->count + trial_steps);
+        st = tkh::ensure_wave(S, S->count + 2 * trial_steps);
         if (st != TK_OK) return bfail(B, st, "tk_batch_tune: %s", S->err);
     }
     // keep every member's state and sample counter, restore them after each trial
@@ -518,15 +531,106 @@ tk_status tk_batch_tune(tk_batch *B, int trial_steps, int *best_seg, double *bes
         }
         cudaStreamSynchronize(B->stream);
     }
+    // The best work-queue pair against the other strategy, the members one
+    // after another through tk_step: each timed on the device at trial_steps
+    // and 2 trial_steps outer steps, and compared by the difference, so that
+    // fixed start-up costs (of each launch sequence, of each member's
+    // cooperative launch and host synchronization), which a long
+    // tk_batch_step amortizes, count for neither.
+    double queue_ms = 1e300;
+    if (st == TK_OK) {
+        B->blocks = best_blocks;
+        st = build_items(B, best);
+        if (st == TK_OK) st = upload_members(B);
+        double t[2] = {0.0, 0.0};
+        for (int r = 0; r < 2 && st == TK_OK; ++r) {
+            cudaEventRecord(e0, B->stream);
+            st = enqueue(B, (r + 1) * trial_steps, B->stream);
+            cudaEventRecord(e1, B->stream);
+            if (st != TK_OK) break;
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            t[r] = ms;
+            for (int k = 0; k < B->n; ++k) {   // undo the trial
+                tk_solver *S = B->mem[k];
+                cudaMemcpyAsync(S->u[S->cur], keep[k], (size_t)S->Nr * 4 * S->NP * S->esz,
+                                cudaMemcpyDeviceToDevice, B->stream);
+                cudaMemcpyAsync(S->ctr, &keep_ctr[k], sizeof(long long), cudaMemcpyHostToDevice, B->stream);
+            }
+            cudaStreamSynchronize(B->stream);
+        }
+        queue_ms = t[1] - t[0];
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    // Only members that each fill the GPU alone (one block per SM in their own
+    // persistent launch) are candidates for the other strategy: smaller ones
+    // are what the work queue is for (24 members of 1601 x 32 run 1.18x
+    // faster through it), and short trials of direct launches understate it.
+    bool all_fill = true;
+    for (tk_solver *S : B->mem) all_fill = all_fill && S->persist && S->warps != tk::kNarrowWarps;
+    bool per_member = false;
+    if (st == TK_OK && all_fill) {
+        std::vector<int> cur0(B->n);
+        std::vector<long long> count0(B->n), done0(B->n);
+        for (int k = 0; k < B->n; ++k) {
+            cur0[k] = B->mem[k]->cur;
+            count0[k] = B->mem[k]->count;
+            done0[k] = B->mem[k]->steps_done;
+        }
+        for (tk_solver *S : B->mem) {
+            st = tkh::ensure_wave(S, S->count + 2 * trial_steps);
+            if (st != TK_OK) {
+                bfail(B, st, "tk_batch_tune: %s", S->err);
+                break;
+            }
+        }
+        cudaEvent_t a0, a1;
+        cudaEventCreate(&a0);
+        cudaEventCreate(&a1);
+        double ms_n[2] = {0.0, 0.0};
+        for (int r = 0; r < 2 && st == TK_OK; ++r) {
+            cudaDeviceSynchronize();
+            for (tk_solver *S : B->mem) {
+                cudaEventRecord(a0, S->stream);
+                st = tk_step(S, (r + 1) * trial_steps);
+                cudaEventRecord(a1, S->stream);
+                if (st != TK_OK) {
+                    bfail(B, st, "tk_batch_tune: %s", S->err);
+                    break;
+                }
+                cudaEventSynchronize(a1);
+                float m = 0.f;
+                cudaEventElapsedTime(&m, a0, a1);
+                ms_n[r] += m;
+            }
+            cudaDeviceSynchronize();
+            for (int k = 0; k < B->n; ++k) {   // undo the trial
+                tk_solver *S = B->mem[k];
+                S->cur = cur0[k];
+                S->count = count0[k];
+                S->steps_done = done0[k];
+                cudaMemcpyAsync(S->u[S->cur], keep[k], (size_t)S->Nr * 4 * S->NP * S->esz,
+                                cudaMemcpyDeviceToDevice, B->stream);
+                cudaMemcpyAsync(S->ctr, &keep_ctr[k], sizeof(long long), cudaMemcpyHostToDevice, B->stream);
+            }
+            cudaStreamSynchronize(B->stream);
+        }
+        cudaEventDestroy(a0);
+        cudaEventDestroy(a1);
+        const double ms = ms_n[1] - ms_n[0];   // trial_steps outer steps without the fixed costs
+        if (st == TK_OK && ms > 0.0 && ms < queue_ms) per_member = true;
+        best_t = per_member ? ms : (queue_ms > 0.0 && queue_ms < 1e300 ? queue_ms : best_t);
+    }
     for (void *p : keep) cudaFree(p);
     B->graph_chunk = old_chunk;
     B->blocks = best_blocks;
     if (st != TK_OK) return st;
     st = build_items(B, best);
     if (st != TK_OK) return st;
-    if (best_seg) *best_seg = best;
+    B->per_member = per_member;
+    if (best_seg) *best_seg = per_member ? 0 : best;
     if (best_ms) *best_ms = best_t / trial_steps;
     TKB_CUDA(B, cudaGetLastError());
     return TK_OK;
@@ -536,8 +640,8 @@ tk_status tk_batch_info(const tk_batch *B, int *kmax, int *seg, int *blocks)
 {
     if (!B) return TK_ERR_ARG;
     if (kmax) *kmax = B->kmax;
-    if (seg) *seg = B->seg;
-    if (blocks) *blocks = B->blocks;
+    if (seg) *seg = B->per_member ? 0 : B->seg;
+    if (blocks) *blocks = B->per_member ? 0 : B->blocks;
     return TK_OK;
 }
 

@@ -60,7 +60,7 @@ def _same(a, b):
         assert len(w1) == len(w2) and all(np.array_equal(x, y) for x, y in zip(w1, w2))
 
 
-@pytest.mark.parametrize("chunk,seg", [(-1, None), (0, 16), (3, 5)])
+@pytest.mark.parametrize("chunk,seg", [(-1, None), (0, 16), (3, 5), (-1, 0)])
 def test_batch_is_bit_identical_to_members_alone(chunk, seg):
     import paper_1010_3816_gb300 as tk
     alone = [_solver(w) for w in MEMBERS]
@@ -92,11 +92,14 @@ def test_autotuner_keeps_state_and_results():
     b.step(5)
     before = _results(batched)
     seg, ms = b.tune(trial_steps=2)
-    assert seg in (4, 8, 12, 16, 24, 32, 48, 64, 96, 128) and ms > 0
+    assert seg in (0, 4, 8, 12, 16, 24, 32, 48, 64, 96, 128) and ms > 0
     assert b.info()["seg"] == seg
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    assert b.info()["blocks"] % sms == 0 and b.info()["blocks"] >= sms   # the tuned grid
+    if seg:                                    # the tuned work-queue grid
+        assert b.info()["blocks"] % sms == 0 and b.info()["blocks"] >= sms
+    else:                                      # the members one after another
+        assert b.info()["blocks"] == 0
     _same(_results(batched), before)          # tuning left every member untouched
     b.step(5)
     for g, _ in alone:
