@@ -466,6 +466,7 @@ def run_adjoint(args, tk, torch, rank, world, local):
     f_clk = (clk.get("sm_mhz") or 2070.0) * 1e6
     peak = NUM_SMS * FP64_FMA_PER_CLK_PER_SM * 2 * f_clk / 1e12
     n_inner = n_outer * w.substeps
+    fwd_persistent = tk.tk_get_steps_per_launch(g.h) == -1
 
     def fp64_roof(kernel, flop, instr, seconds):
         launch_s = seconds / n_inner
@@ -505,10 +506,12 @@ def run_adjoint(args, tk, torch, rank, world, local):
             "roofline_adjoint": fp64_roof("lw_adjoint_kernel<double>", ADJ_FLOP_PER_UPDATE,
                                           ADJ_INSTR_PER_UPDATE, bwd),
             "grad": [float(x) for x in grads], "param_gradient": pgrad,
-            "roofline": fp64_roof("lw_step_kernel<double>", FP64_FLOP_PER_UPDATE,
-                                  FP64_INSTR_PER_UPDATE, fwd),
+            "roofline": fp64_roof("lw_persistent_kernel<double>" if fwd_persistent else "lw_step_kernel<double>",
+                                  FP64_FLOP_PER_UPDATE, FP64_INSTR_PER_UPDATE, fwd),
             "cpu_baseline": None, "e2e": None, "clocks": clk,
-            "gpu_launches": args.steps * 2 * (n_outer * w.substeps),
+            # per timed step: the forward solve (one persistent launch, or one
+            # launch per inner step) and one adjoint launch per inner step
+            "gpu_launches": args.steps * ((1 if fwd_persistent else n_inner) + n_inner),
         }
         print(json.dumps(line))
     g.close()
