@@ -503,15 +503,16 @@ def run_adjoint(args, tk, torch, rank, world, local):
                        "gradient_wrt": ["amplitude", "centre", "width", "initial planes"],
                        "parallelism": "single GPU", "l2": L2_NOTE},
             "forward_updates_per_s": inner / fwd, "adjoint_updates_per_s": inner / bwd,
-            "roofline_adjoint": fp64_roof("lw_adjoint_kernel<double>", ADJ_FLOP_PER_UPDATE,
+            "roofline_adjoint": fp64_roof("lw_adjoint_persistent_kernel<double>" if fwd_persistent
+                                          else "lw_adjoint_kernel<double>", ADJ_FLOP_PER_UPDATE,
                                           ADJ_INSTR_PER_UPDATE, bwd),
             "grad": [float(x) for x in grads], "param_gradient": pgrad,
             "roofline": fp64_roof("lw_persistent_kernel<double>" if fwd_persistent else "lw_step_kernel<double>",
                                   FP64_FLOP_PER_UPDATE, FP64_INSTR_PER_UPDATE, fwd),
             "cpu_baseline": None, "e2e": None, "clocks": clk,
-            # per timed step: the forward solve (one persistent launch, or one
-            # launch per inner step) and one adjoint launch per inner step
-            "gpu_launches": args.steps * ((1 if fwd_persistent else n_inner) + n_inner),
+            # per timed step: the forward solve and the adjoint sweep, each one
+            # persistent launch, or one launch per inner step
+            "gpu_launches": args.steps * (2 if fwd_persistent else 2 * n_inner),
         }
         print(json.dumps(line))
     g.close()

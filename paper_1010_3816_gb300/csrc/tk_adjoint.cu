@@ -38,20 +38,21 @@ struct InjectArgs {
 };
 
 // Load the adjoint state of column i, add the gradient of the waveform sample
-// taken at this column (if any), and zero it on the radial edges.
+// `sample` taken at this column (if `on` and the column holds an observer),
+// and zero it on the radial edges.
 template <typename T, int K>
 __device__ __forceinline__ void load_lam(const T *__restrict__ lam, int i, int Nr, int lane,
-                                         const InjectArgs &inj, T (&l)[4][K])
+                                         const InjectArgs &inj, int on, long long sample, T (&l)[4][K])
 {
     constexpr int NP = 32 * K;
     load_col<T, K>(lam + (size_t)i * 4 * NP + lane * K, l);
-    if (inj.on) {
+    if (on) {
         for (int k = 0; k < inj.obs.n; ++k) {
             const int slot = (i == inj.obs.i0[k]) ? 0 : ((i == inj.obs.i0[k] + 1) ? 1 : -1);
             if (slot < 0) continue;
             const int j0 = inj.obs.j0[k];
             const double wr = slot ? inj.obs.wr1[k] : inj.obs.wr0[k];
-            const double *g = inj.dwave + ((size_t)k * inj.count + inj.sample) * 2;
+            const double *g = inj.dwave + ((size_t)k * inj.count + sample) * 2;
             const double gr = g[0], gi = g[1];
 #pragma unroll
             for (int t = 0; t < K; ++t) {
@@ -240,11 +241,11 @@ lw_adjoint_kernel(const T *__restrict__ lam, T *__restrict__ mu_out, const T *__
 #pragma unroll
     for (int t = 0; t < K; ++t) ymr[t] = ymi[t] = T(0);
     if (i1 > i0) {
-        load_lam<T, K>(lam, i0, Nr, lane, inj, la);
+        load_lam<T, K>(lam, i0, Nr, lane, inj, inj.on, inj.sample, la);
         node_z<T, K>(node + (size_t)i0 * NQ + row, la, zar, zai);
         if (lead && i0 > 0) {
             T ll[4][K], zlr[K], zli[K];
-            load_lam<T, K>(lam, i0 - 1, Nr, lane, inj, ll);
+            load_lam<T, K>(lam, i0 - 1, Nr, lane, inj, inj.on, inj.sample, ll);
             node_z<T, K>(node + (size_t)(i0 - 1) * NQ + row, ll, zlr, zli);
             eta_half<T, K>(ll, la, zlr, zli, zar, zai, node + (size_t)(i0 - 1) * NQ + row,
                            node + (size_t)i0 * NQ + row, en, em);
@@ -253,7 +254,7 @@ lw_adjoint_kernel(const T *__restrict__ lam, T *__restrict__ mu_out, const T *__
         for (int i = i0; i < i1; ++i) {
             T lc[4][K], zcr[K], zci[K], ep[4][K], ypr[K], ypi[K];
             if (i + 1 < Nr) {
-                load_lam<T, K>(lam, i + 1, Nr, lane, inj, lc);
+                load_lam<T, K>(lam, i + 1, Nr, lane, inj, inj.on, inj.sample, lc);
                 node_z<T, K>(node + (size_t)(i + 1) * NQ + row, lc, zcr, zci);
                 eta_half<T, K>(la, lc, zar, zai, zcr, zci, node + (size_t)i * NQ + row,
                                node + (size_t)(i + 1) * NQ + row, en, ep);
@@ -324,6 +325,186 @@ lw_adjoint_kernel(const T *__restrict__ lam, T *__restrict__ mu_out, const T *__
         mu_node<T, K>(l0, ep, el, ypr, ypi, yml, ymli, half + (size_t)i0 * HP + row,
                       half + (size_t)(i0 - 1) * HP + row, mu);
         store_col<T, K>(mu_out + (size_t)i0 * SP + row, mu);
+    }
+}
+
+// Every adjoint step of a tk_adjoint call in one cooperative launch, with the
+// dataflow of the forward persistent sweep (step_sweep_async): no barrier
+// between steps; each warp waits (bounded) only for its two siblings and, at
+// a block's edges, the neighbouring block's edge warp.  Step s:
+//   - first phase (every half node and node that involves only the block's
+//     columns): it reads the right sibling's first column and overwrites its
+//     own last half node, which that sibling read in the last step, so it
+//     waits until that sibling has finished step s - 1;
+//   - the block's last warp waits until the right neighbouring block's first
+//     warp has finished step s - 1, then forms its last column;
+//   - the deferred first node: the block's first warp waits until the left
+//     neighbouring block's last warp has finished step s - 1 and forms its
+//     left half node from that warp's column; every other warp takes its left
+//     sibling's last half node once that sibling's first phase is done.
+// Same arithmetic on the same operands as lw_adjoint_kernel.
+template <typename T, int K, int W>
+__device__ __forceinline__ void adj_sweep_async(unsigned char *sh_raw, const T *__restrict__ lam,
+                                                T *__restrict__ mu_out, const T *__restrict__ half,
+                                                const T *__restrict__ node, int Nr, T en, const InjectArgs &inj,
+                                                int on, long long sample, unsigned int *flags,
+                                                unsigned int *first_done, unsigned int *step_done, unsigned int s,
+                                                int *err)
+{
+    constexpr int NP = 32 * K;
+    constexpr size_t SP = 4 * NP, HP = (size_t)kNCH * NP, NQ = (size_t)kNCN * NP;
+    T(*sh)[kAdjShared][NP] = reinterpret_cast<T(*)[kAdjShared][NP]>(sh_raw);
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int i0, i1, left;
+    warp_range<W>(Nr, wib, &i0, &i1, &left);
+    // at most Nr / W blocks: every warp has a column (as in step_sweep_async)
+    if (i1 <= i0) return;
+    const int row = lane * K;
+    const bool lead = (left < 0);
+    const int b1 = (int)(((long long)(blockIdx.x + 1) * Nr) / gridDim.x);
+    const bool last = (i1 == b1);
+    const int iend = last ? i1 - 1 : i1;
+    const unsigned int nb = gridDim.x;
+    if (s > 0 && !last) warp_wait_cta(&step_done[wib + 1], s, err);
+
+    T la[4][K], zar[K], zai[K];        // node i: lam~ and its neighbour sources
+    T em[4][K], ymr[K], ymi[K];        // half node i-1/2: eta and its neighbour sources
+    zero_col<T, K>(em);
+#pragma unroll
+    for (int t = 0; t < K; ++t) ymr[t] = ymi[t] = T(0);
+    load_lam<T, K>(lam, i0, Nr, lane, inj, on, sample, la);
+    node_z<T, K>(node + (size_t)i0 * NQ + row, la, zar, zai);
+    // the right half node of column i (from column i + 1) and, for i > i0, its node
+    auto column = [&](int i) {
+        T lc[4][K], zcr[K], zci[K], ep[4][K], ypr[K], ypi[K];
+        if (i + 1 < Nr) {
+            load_lam<T, K>(lam, i + 1, Nr, lane, inj, on, sample, lc);
+            node_z<T, K>(node + (size_t)(i + 1) * NQ + row, lc, zcr, zci);
+            eta_half<T, K>(la, lc, zar, zai, zcr, zci, node + (size_t)i * NQ + row,
+                           node + (size_t)(i + 1) * NQ + row, en, ep);
+            half_y<T, K>(half + (size_t)i * HP + row, ep, ypr, ypi);
+        } else {
+            zero_col<T, K>(lc);
+            zero_col<T, K>(ep);
+#pragma unroll
+            for (int t = 0; t < K; ++t) zcr[t] = zci[t] = ypr[t] = ypi[t] = T(0);
+        }
+        if (i == i0) {
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    sh[wib][6 + c][row + t] = la[c][t];
+                    sh[wib][10 + c][row + t] = ep[c][t];
+                }
+                sh[wib][14][row + t] = ypr[t];
+                sh[wib][15][row + t] = ypi[t];
+            }
+        } else {
+            T mu[4][K];
+            mu_node<T, K>(la, ep, em, ypr, ypi, ymr, ymi, half + (size_t)i * HP + row,
+                          half + (size_t)(i - 1) * HP + row, mu);
+            store_col<T, K>(mu_out + (size_t)i * SP + row, mu);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+                la[c][t] = lc[c][t];
+                em[c][t] = ep[c][t];
+            }
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+            zar[t] = zcr[t];
+            zai[t] = zci[t];
+            ymr[t] = ypr[t];
+            ymi[t] = ypi[t];
+        }
+    };
+    for (int i = i0; i < iend; ++i) column(i);
+    if (!last)   // eta at i1 - 1/2 with its sources: the right sibling's left edge
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sh[wib][c][row + t] = em[c][t];
+            sh[wib][4][row + t] = ymr[t];
+            sh[wib][5][row + t] = ymi[t];
+        }
+    warp_publish_cta(&first_done[wib], s + 1);
+    if (last) {
+        if (s > 0 && blockIdx.x + 1 < nb) warp_wait_flag(flags + blockIdx.x + 1, s, err);
+        column(i1 - 1);
+        __syncwarp();
+    }
+    {   // the deferred first node
+        T l0[4][K], ep[4][K], el[4][K], ypr[K], ypi[K], yml[K], ymli[K], mu[4][K];
+#pragma unroll
+        for (int t = 0; t < K; ++t) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                l0[c][t] = sh[wib][6 + c][row + t];
+                ep[c][t] = sh[wib][10 + c][row + t];
+            }
+            ypr[t] = sh[wib][14][row + t];
+            ypi[t] = sh[wib][15][row + t];
+        }
+        if (lead) {
+            if (s > 0 && blockIdx.x > 0) warp_wait_flag(flags + nb + blockIdx.x - 1, s, err);
+            if (i0 > 0) {
+                T ll[4][K], zlr[K], zli[K], z0r[K], z0i[K];
+                load_lam<T, K>(lam, i0 - 1, Nr, lane, inj, on, sample, ll);
+                node_z<T, K>(node + (size_t)(i0 - 1) * NQ + row, ll, zlr, zli);
+                node_z<T, K>(node + (size_t)i0 * NQ + row, l0, z0r, z0i);
+                eta_half<T, K>(ll, l0, zlr, zli, z0r, z0i, node + (size_t)(i0 - 1) * NQ + row,
+                               node + (size_t)i0 * NQ + row, en, el);
+                half_y<T, K>(half + (size_t)(i0 - 1) * HP + row, el, yml, ymli);
+            } else {
+                zero_col<T, K>(el);
+#pragma unroll
+                for (int t = 0; t < K; ++t) yml[t] = ymli[t] = T(0);
+            }
+        } else {
+            warp_wait_cta(&first_done[left], s + 1, err);
+#pragma unroll
+            for (int t = 0; t < K; ++t) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) el[c][t] = sh[left][c][row + t];
+                yml[t] = sh[left][4][row + t];
+                ymli[t] = sh[left][5][row + t];
+            }
+        }
+        mu_node<T, K>(l0, ep, el, ypr, ypi, yml, ymli, half + (size_t)i0 * HP + row,
+                      half + (size_t)(i0 > 0 ? i0 - 1 : 0) * HP + row, mu);
+        store_col<T, K>(mu_out + (size_t)i0 * SP + row, mu);
+    }
+    if (lead) warp_publish_gpu(flags + blockIdx.x, s + 1);
+    if (last) warp_publish_gpu(flags + nb + blockIdx.x, s + 1);
+    warp_publish_cta(&step_done[wib], s + 1);
+}
+
+// Launch step s is the transpose of inner step n_inner - 1 - s: the gradient
+// of sample count - 1 - s / substeps is injected at its first sub-step.  The
+// adjoint state starts in a0; the result is in a0 or a1 by the parity of
+// n_inner.
+template <typename T, int K, int W>
+__global__ void __launch_bounds__(W * 32, adj_wide_warps<T, K>() / W)
+lw_adjoint_persistent_kernel(T *a0, T *a1, const T *__restrict__ half, const T *__restrict__ node, int Nr,
+                             T en, const InjectArgs inj, int inject, long long n_inner, int substeps,
+                             unsigned int *flags, int *err)
+{
+    extern __shared__ __align__(16) unsigned char sh_raw[];
+    __shared__ unsigned int first_done[W], step_done[W];
+    if (threadIdx.x < W) {
+        first_done[threadIdx.x] = 0;
+        step_done[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (long long s = 0; s < n_inner; ++s) {
+        const T *lam = (s & 1) ? a1 : a0;
+        T *mu = (s & 1) ? a0 : a1;
+        adj_sweep_async<T, K, W>(sh_raw, lam, mu, half, node, Nr, en, inj, inject && (s % substeps == 0),
+                                 inj.count - 1 - s / substeps, flags, first_done, step_done, (unsigned)s, err);
     }
 }
 
@@ -412,7 +593,7 @@ param_tangent_kernel(const double *__restrict__ u, const double *__restrict__ la
                 double d1[4][K], d2[4][K], l[4][K];
                 full_node<double, K>(hm, hp, zero, dnode + (size_t)i * NQ + row, 0.0, d1);
                 full_node<double, K>(dm, dp, zero, node + (size_t)i * NQ + row, en, d2);
-                load_lam<double, K>(lam, i, Nr, lane, inj, l);
+                load_lam<double, K>(lam, i, Nr, lane, inj, inj.on, inj.sample, l);
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -550,6 +731,100 @@ cudaError_t launch_adjoint_step(int precision, int K, const void *lam, void *mu,
 }
 
 template <typename T, int K, int W>
+int adj_persistent_blocks_w(int Nr, int num_sms)
+{
+    static cudaError_t e0 = cudaFuncSetAttribute(lw_adjoint_persistent_kernel<T, K, W>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)adj_smem_bytes<T, K, W>());
+    int n = 0;
+    if (e0 != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, lw_adjoint_persistent_kernel<T, K, W>, W * 32,
+                                                      adj_smem_bytes<T, K, W>()) != cudaSuccess ||
+        n < 1)
+        return 0;
+    long long blocks = (long long)num_sms * n;
+    if (blocks > Nr / W) blocks = Nr / W;
+    return blocks < 1 ? 0 : (int)blocks;
+}
+
+template <typename T, int K>
+int adj_persistent_blocks_t(int Nr, int num_sms, int warps)
+{
+    constexpr int WW = adj_wide_warps<T, K>();
+    if (warps == WW) return adj_persistent_blocks_w<T, K, WW>(Nr, num_sms);
+    if (warps == kNarrowWarps) return adj_persistent_blocks_w<T, K, kNarrowWarps>(Nr, num_sms);
+    return 0;
+}
+
+template <typename T, int K, int W>
+cudaError_t launch_adj_persistent_w(void *a0, void *a1, const void *half, const void *node, int Nr, int blocks,
+                                    double dt_in, const InjectArgs &inj, int inject, long long n_inner,
+                                    int substeps, unsigned int *flags, int *err, cudaStream_t st)
+{
+    T *p0 = (T *)a0, *p1 = (T *)a1;
+    const T *h = (const T *)half, *nd = (const T *)node;
+    T en = (T)(0.5 * dt_in);
+    InjectArgs in = inj;
+    void *args[] = {&p0, &p1, &h, &nd, &Nr, &en, &in, &inject, &n_inner, &substeps, &flags, &err};
+    return cudaLaunchCooperativeKernel((const void *)lw_adjoint_persistent_kernel<T, K, W>, dim3(blocks),
+                                       dim3(W * 32), args, adj_smem_bytes<T, K, W>(), st);
+}
+
+template <typename T, int K>
+cudaError_t launch_adj_persistent_t(void *a0, void *a1, const void *half, const void *node, int Nr, int blocks,
+                                    int warps, double dt_in, const InjectArgs &inj, int inject,
+                                    long long n_inner, int substeps, unsigned int *flags, int *err,
+                                    cudaStream_t st)
+{
+    constexpr int WW = adj_wide_warps<T, K>();
+    if (warps == WW)
+        return launch_adj_persistent_w<T, K, WW>(a0, a1, half, node, Nr, blocks, dt_in, inj, inject, n_inner,
+                                                 substeps, flags, err, st);
+    if (warps == kNarrowWarps)
+        return launch_adj_persistent_w<T, K, kNarrowWarps>(a0, a1, half, node, Nr, blocks, dt_in, inj, inject,
+                                                           n_inner, substeps, flags, err, st);
+    return cudaErrorInvalidValue;
+}
+
+// Blocks of the persistent adjoint launch for this grid (all resident at
+// once, at most Nr / warps), or 0 if it cannot run.
+int adjoint_persistent_blocks(int precision, int K, int Nr, int num_sms, int warps)
+{
+    if (precision == 0)
+        return K == 1 ? adj_persistent_blocks_t<double, 1>(Nr, num_sms, warps)
+             : K == 2 ? adj_persistent_blocks_t<double, 2>(Nr, num_sms, warps)
+                      : adj_persistent_blocks_t<double, 4>(Nr, num_sms, warps);
+    return K == 1 ? adj_persistent_blocks_t<float, 1>(Nr, num_sms, warps)
+         : K == 2 ? adj_persistent_blocks_t<float, 2>(Nr, num_sms, warps)
+                  : adj_persistent_blocks_t<float, 4>(Nr, num_sms, warps);
+}
+
+cudaError_t launch_adjoint_persistent(int precision, int K, void *a0, void *a1, const void *half,
+                                      const void *node, int Nr, int blocks, int warps, double dt_in,
+                                      const InjectArgs &inj, int inject, long long n_inner, int substeps,
+                                      unsigned int *flags, int *err, cudaStream_t st)
+{
+    if (precision == 0) {
+        if (K == 1)
+            return launch_adj_persistent_t<double, 1>(a0, a1, half, node, Nr, blocks, warps, dt_in, inj, inject,
+                                                      n_inner, substeps, flags, err, st);
+        if (K == 2)
+            return launch_adj_persistent_t<double, 2>(a0, a1, half, node, Nr, blocks, warps, dt_in, inj, inject,
+                                                      n_inner, substeps, flags, err, st);
+        return launch_adj_persistent_t<double, 4>(a0, a1, half, node, Nr, blocks, warps, dt_in, inj, inject,
+                                                  n_inner, substeps, flags, err, st);
+    }
+    if (K == 1)
+        return launch_adj_persistent_t<float, 1>(a0, a1, half, node, Nr, blocks, warps, dt_in, inj, inject,
+                                                 n_inner, substeps, flags, err, st);
+    if (K == 2)
+        return launch_adj_persistent_t<float, 2>(a0, a1, half, node, Nr, blocks, warps, dt_in, inj, inject,
+                                                 n_inner, substeps, flags, err, st);
+    return launch_adj_persistent_t<float, 4>(a0, a1, half, node, Nr, blocks, warps, dt_in, inj, inject,
+                                             n_inner, substeps, flags, err, st);
+}
+
+template <typename T, int K, int W>
 int adj_resident()
 {
     int n = 0;
@@ -664,14 +939,46 @@ extern "C" tk_status tk_adjoint(tk_solver *S, const double *dL_dwave, const doub
     }
     int cur = 0;
     const double dt_in = S->dt / S->substeps;
-    for (long long t = count - 1; t >= 0 && e == cudaSuccess; --t)
-        for (int k = 0; k < S->substeps && e == cudaSuccess; ++k) {
-            inj.on = (k == 0) && dwave != nullptr;
-            inj.sample = t;
-            e = tk::launch_adjoint_step(S->precision, S->K, S->adj[cur], S->adj[cur ^ 1], S->half,
-                                        S->node, S->Nr, S->adj_blocks, S->adj_warps, dt_in, inj, S->stream);
-            cur ^= 1;
+    const long long n_inner = count * S->substeps;
+    // the solver's launch structure: every step in one persistent launch, or
+    // one launch per step
+    const int pblocks = (S->persist && n_inner > 0)
+                            ? tk::adjoint_persistent_blocks(S->precision, S->K, S->Nr, S->num_sms, S->adj_warps)
+                            : 0;
+    if (pblocks > 0 && e == cudaSuccess) {
+        unsigned int *flags = nullptr;
+        const size_t fbytes = (size_t)2 * pblocks * sizeof(unsigned int) + sizeof(int);
+        st = tkh::alloc(S, (void **)&flags, fbytes);
+        if (st != TK_OK) {
+            cleanup();
+            return st;
         }
+        int *derr = (int *)(flags + 2 * pblocks);
+        int herr = 0;
+        e = cudaMemsetAsync(flags, 0, fbytes, S->stream);
+        if (e == cudaSuccess)
+            e = tk::launch_adjoint_persistent(S->precision, S->K, S->adj[0], S->adj[1], S->half, S->node, S->Nr,
+                                              pblocks, S->adj_warps, dt_in, inj, dwave != nullptr, n_inner,
+                                              S->substeps, flags, derr, S->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, S->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->stream);
+        cudaFree(flags);
+        if (e == cudaSuccess && herr) {
+            cleanup();
+            return tkh::fail(S, TK_ERR_INTERNAL, "tk_adjoint: a block of the persistent launch waited too "
+                                                 "long for a neighbour; the gradient is invalid");
+        }
+        cur = (int)(n_inner & 1);
+    } else {
+        for (long long t = count - 1; t >= 0 && e == cudaSuccess; --t)
+            for (int k = 0; k < S->substeps && e == cudaSuccess; ++k) {
+                inj.on = (k == 0) && dwave != nullptr;
+                inj.sample = t;
+                e = tk::launch_adjoint_step(S->precision, S->K, S->adj[cur], S->adj[cur ^ 1], S->half,
+                                            S->node, S->Nr, S->adj_blocks, S->adj_warps, dt_in, inj, S->stream);
+                cur ^= 1;
+            }
+    }
     if (e != cudaSuccess) {
         cleanup();
         return tkh::fail(S, TK_ERR_CUDA, "tk_adjoint: %s", cudaGetErrorString(e));

@@ -554,5 +554,82 @@ __device__ __forceinline__ void observe(int i, int lane, const T (&o)[4][K], con
     }
 }
 
+// Bounded waits of the persistent kernels.  A wait gives up after kMaxSpins
+// polls (about 8.6 s on GB300), or at once when *err is already set, and
+// sets *err; the launch then ends and the host reports the error.
+constexpr long long kMaxSpins = 1ll << 24;
+
+__device__ __forceinline__ unsigned int load_acquire(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// A whole warp waits (bounded) until *flag >= epoch; every lane reads the
+// flag with acquire semantics, and the lanes leave together.
+__device__ __forceinline__ void warp_wait_flag(const unsigned int *flag, unsigned int epoch, int *err,
+                                               long long max_spins = kMaxSpins)
+{
+    long long spins = 0;
+    while (!__all_sync(0xffffffffu, load_acquire(flag) >= epoch)) {
+        if (__any_sync(0xffffffffu, ++spins > max_spins || *(volatile int *)err != 0)) {
+            if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
+            return;
+        }
+        __nanosleep(64);
+    }
+}
+
+// Progress counters between the warps of a block, in shared memory: a
+// release store after the warp's writes, acquire loads by the waiting warp.
+__device__ __forceinline__ void cta_release(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)),
+                 "r"(v)
+                 : "memory");
+}
+
+__device__ __forceinline__ unsigned int cta_acquire(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];"
+                 : "=r"(v)
+                 : "r"((unsigned)__cvta_generic_to_shared(p))
+                 : "memory");
+    return v;
+}
+
+// A whole warp waits (bounded) until the shared counter *c >= v.
+__device__ __forceinline__ void warp_wait_cta(const unsigned int *c, unsigned int v, int *err,
+                                              long long max_spins = kMaxSpins)
+{
+    long long spins = 0;
+    while (!__all_sync(0xffffffffu, cta_acquire(c) >= v)) {
+        if (__any_sync(0xffffffffu, ++spins > max_spins || *(volatile int *)err != 0)) {
+            if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
+            return;
+        }
+        __nanosleep(32);
+    }
+}
+
+// The warp's writes so far are visible to the block (cta) or to the GPU
+// before the counter or flag says so.
+__device__ __forceinline__ void warp_publish_cta(unsigned int *c, unsigned int v)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) cta_release(c, v);
+}
+
+__device__ __forceinline__ void warp_publish_gpu(unsigned int *f, unsigned int v)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence();
+        atomicExch(f, v);
+    }
+}
+
 }  // namespace
 }  // namespace tk

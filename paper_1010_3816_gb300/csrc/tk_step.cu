@@ -207,28 +207,9 @@ lw_step_kernel(const T *__restrict__ u_in, T *__restrict__ u_out, const T *__res
     if (wa.write) advance_sample(wa);
 }
 
-// Many Lax-Wendroff steps in one launch, for grids too small to fill the GPU
-// with long sweeps, where per-launch overhead would dominate.  All blocks are
-// resident at once (cooperative launch).  There is no barrier between steps:
-// each warp waits only for the warps whose data it reads or overwrites -- its
-// two siblings in the block, and for a block's first and last warp the edge
-// warp of the neighbouring block -- through counters of finished steps
-// (step_sweep_async).  Every wait is bounded: after kMaxSpins polls the warp
-// sets *err, and from then on every wait returns at once, so this kernel runs
-// its remaining steps without waiting and the persistent kernels below leave
-// their loops (the state is then invalid and the host reports the error).
-// State loads go
-// through L2 (other blocks write them).  u0 holds u^n at the start; the result
-// is in u0 or u1 by the parity of n_inner.
-constexpr long long kMaxSpins = 1ll << 24;
-
-__device__ __forceinline__ unsigned int load_acquire(const unsigned int *p)
-{
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
+// The blocks' neighbour barrier of the ring and four-step sweeps: the block
+// publishes epoch and waits (bounded, by thread 0) until both neighbouring
+// blocks have published it; false if a wait ran out.
 __device__ __forceinline__ bool neighbour_barrier(unsigned int *flags, unsigned int epoch, int *err,
                                                   long long max_spins = kMaxSpins)
 {
@@ -257,70 +238,6 @@ __device__ __forceinline__ bool neighbour_barrier(unsigned int *flags, unsigned 
     return ok != 0;
 }
 
-// A whole warp waits (bounded) until *flag >= epoch; every lane reads the
-// flag with acquire semantics, and the lanes leave together.
-__device__ __forceinline__ void warp_wait_flag(const unsigned int *flag, unsigned int epoch, int *err,
-                                               long long max_spins = kMaxSpins)
-{
-    long long spins = 0;
-    while (!__all_sync(0xffffffffu, load_acquire(flag) >= epoch)) {
-        if (__any_sync(0xffffffffu, ++spins > max_spins || *(volatile int *)err != 0)) {
-            if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
-            return;
-        }
-        __nanosleep(64);
-    }
-}
-
-// Progress counters between the warps of a block, in shared memory: a
-// release store after the warp's writes, acquire loads by the waiting warp.
-__device__ __forceinline__ void cta_release(unsigned int *p, unsigned int v)
-{
-    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)),
-                 "r"(v)
-                 : "memory");
-}
-
-__device__ __forceinline__ unsigned int cta_acquire(const unsigned int *p)
-{
-    unsigned int v;
-    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];"
-                 : "=r"(v)
-                 : "r"((unsigned)__cvta_generic_to_shared(p))
-                 : "memory");
-    return v;
-}
-
-// A whole warp waits (bounded) until the shared counter *c >= v.
-__device__ __forceinline__ void warp_wait_cta(const unsigned int *c, unsigned int v, int *err,
-                                              long long max_spins = kMaxSpins)
-{
-    long long spins = 0;
-    while (!__all_sync(0xffffffffu, cta_acquire(c) >= v)) {
-        if (__any_sync(0xffffffffu, ++spins > max_spins || *(volatile int *)err != 0)) {
-            if ((threadIdx.x & 31) == 0) atomicExch(err, 1);
-            return;
-        }
-        __nanosleep(32);
-    }
-}
-
-// The warp's writes so far are visible to the block (cta) or to the GPU
-// before the counter or flag says so.
-__device__ __forceinline__ void warp_publish_cta(unsigned int *c, unsigned int v)
-{
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) cta_release(c, v);
-}
-
-__device__ __forceinline__ void warp_publish_gpu(unsigned int *f, unsigned int v)
-{
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) {
-        __threadfence();
-        atomicExch(f, v);
-    }
-}
 
 // One step of the persistent sweep with no block barrier: every warp waits
 // only for what it uses.  Counters (number of finished steps, or of steps
@@ -472,6 +389,17 @@ __device__ __forceinline__ void step_sweep_async(unsigned char *sh_raw, const T 
     warp_publish_cta(&step_done[wib], s + 1);
 }
 
+// Every Lax-Wendroff step of a call in one launch (the FP64 default).  All
+// blocks are resident at once (cooperative launch).  There is no barrier between steps:
+// each warp waits only for the warps whose data it reads or overwrites -- its
+// two siblings in the block, and for a block's first and last warp the edge
+// warp of the neighbouring block -- through counters of finished steps
+// (step_sweep_async).  Every wait is bounded: after kMaxSpins polls the warp
+// sets *err, and from then on every wait returns at once, so this kernel runs
+// its remaining steps without waiting and the persistent kernels below leave
+// their loops (the state is then invalid and the host reports the error).
+// State loads go through L2 (other blocks write them).  u0 holds u^n at the start; the result
+// is in u0 or u1 by the parity of n_inner.
 template <typename T, int K, int W>
 __global__ void __launch_bounds__(W * 32, wide_warps<T, K>() / W)
 lw_persistent_kernel(T *u0, T *u1, const T *__restrict__ half, const T *__restrict__ node, int Nr,

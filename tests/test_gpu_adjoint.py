@@ -179,3 +179,35 @@ def test_dot_product_full_size_adjoint_grid():
     scale = float(np.sum(np.abs(dwave * waves)) + np.sum(np.abs(dfin * final)))
     assert abs(lhs - rhs) <= 1e-12 * scale, (lhs, rhs, scale)
     g.close()
+
+
+@pytest.mark.parametrize("kw,indep", [
+    (dict(), True),
+    (dict(Ntheta=64, substeps=3, a=0.9), False),
+    (dict(Ntheta=128, Nr=201, substeps=4, m=3), True),
+    (dict(variable=0, m=-1, dt=0.02), False),
+    (dict(Nr=2561, Ntheta=64, substeps=2, rs_max=130.0, steps=12), True),   # one 16-warp block per SM
+    (dict(Nr=3701, Ntheta=32, rs_max=200.0, steps=10), False),               # one 24-warp block per SM
+])
+def test_persistent_adjoint_is_bit_identical_to_one_launch_per_step(kw, indep):
+    """By default tk_adjoint runs every transposed step in one persistent
+    launch (as tk_step runs the forward steps); with one launch per step set
+    it launches each transposed step alone.  Same gradient, bit for bit."""
+    import paper_1010_3816_gb300 as tk
+    w = BASE.with_(**kw)
+    np_ = 4 if indep else 2
+    u0 = _edge0(_rand((np_, w.Ntheta, w.Nr), 31))
+    dwave = _rand((len(w.observers), w.steps, 2), 32)
+    dfin = _rand((4, w.Ntheta, w.Nr), 33)
+    grads = []
+    for spl in (-1, 1):
+        g = _solver(w)
+        g.set_steps_per_launch(spl)
+        assert tk.tk_get_steps_per_launch(g.h) == spl
+        _forward(g, w, u0)
+        grad = np.zeros((np_, w.Ntheta, w.Nr))
+        g.adjoint(grad, dL_dwave=dwave, dL_dfinal=dfin, independent_pi=indep)
+        grads.append(grad)
+        g.close()
+    assert np.isfinite(grads[0]).all() and np.abs(grads[0]).max() > 0
+    assert np.array_equal(grads[0], grads[1])
