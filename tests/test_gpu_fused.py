@@ -126,6 +126,9 @@ PERSISTENT_CASES = [
     (1, _grid(1601, 32, substeps=2), (13, 8)),
     (0, _grid(23, 8, substeps=1, observers=((-30.0, 1.5), (-29.0, 0.5))), (31,)),  # few columns
     (0, _grid(2501, 64, substeps=2), (6, 3)),               # FP64, one 16-warp block per SM
+    (0, _grid(3701, 32, substeps=1), (7, 2)),               # FP64, one 24-warp block per SM (K = 1)
+    (0, _grid(1301, 128, substeps=4), (3, 1)),              # FP64, one 8-warp block per SM (K = 4)
+    (0, _grid(25601, 64, substeps=2), (2,)),                # FP64, the benchmark's grid
     (1, _grid(3001, 64, substeps=2), (7, 1, 4)),            # FP32 pairs, one 12-warp block per SM
     (1, _grid(3001, 64, substeps=3), (5,)),                 # FP32, an odd last step
     (1, _grid(5003, 32, substeps=1), (9,)),                 # FP32 K = 1
@@ -151,9 +154,10 @@ PERSISTENT_CASES = [
                          ids=[f"case{k}" for k in range(len(PERSISTENT_CASES))])
 def test_persistent_launch_bit_identical(precision, w, calls):
     """All inner steps of each tk_step call in one cooperative launch (FP64:
-    single steps; FP32: sweeps of four steps on large grids, then pairs of
-    steps), blocks waiting on their neighbours in between: the same bits as
-    one launch per step, waveforms included."""
+    single steps, each warp waiting only for the warps it depends on; FP32:
+    sweeps of four steps on large grids, then pairs of steps, blocks waiting on
+    their neighbours in between): the same bits as one launch per step,
+    waveforms included."""
     s1, w1 = _run(w, precision, 1, calls)
     sp, wp = _run(w, precision, -1, calls)
     assert np.isfinite(s1).all()
