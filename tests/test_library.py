@@ -51,6 +51,11 @@ def test_argument_validation_without_gpu(lib):
     # calls on a NULL solver fail cleanly
     assert lib.tk_step(None, 1) == tk.TK_ERR_ARG
     assert lib.tk_check_finite(None) == tk.TK_ERR_ARG
+    v = C.c_int(7)
+    assert lib.tk_get_steps_per_launch(None, C.byref(v)) == tk.TK_ERR_ARG and v.value == 7
+    assert lib.tk_get_substeps(None, C.byref(v)) == tk.TK_ERR_ARG
+    assert lib.tk_get_coefficients(None, None, None, 0) == tk.TK_ERR_ARG
+    assert lib.tk_set_coefficients(None, 0.0, 1.0, -2, 2, None, None, None, 0) == tk.TK_ERR_ARG
     lib.tk_destroy(None)
 
 
