@@ -163,7 +163,11 @@ tk_status tk_add_observer(tk_solver *S, double rstar_obs, double theta_obs, int 
  * outer step.  In the persistent mode of tk_set_steps_per_launch (-1, the
  * default) every step of the call runs in one cooperative launch and the call
  * synchronizes the stream to check that launch's bounded waits; in the other
- * modes it is asynchronous.  If one ran out, tk_step returns TK_ERR_INTERNAL,
+ * modes it is asynchronous.  The persistent launch needs all its blocks
+ * resident at once, as the grid was sized for at tk_make_grid; where fewer
+ * fit (a limit on active threads set for the process) the launch fails with
+ * TK_ERR_CUDA and nothing is stepped, and tk_set_steps_per_launch(S, 1) runs
+ * the same steps one launch at a time.  If one ran out, tk_step returns TK_ERR_INTERNAL,
  * the step and sample counts stay where the call found them (the samples
  * taken before it stay readable), and the state is invalid: tk_step,
  * tk_get_state, tk_check_finite, tk_adjoint and tk_param_gradient return
