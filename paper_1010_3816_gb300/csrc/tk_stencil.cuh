@@ -182,11 +182,16 @@ __device__ __forceinline__ void warp_range(int Nr, int wib, int *i0, int *i1, in
     *left = prev;
 }
 
-// FP32 with an even number of rows per lane: the rows go in pairs through
-// GB300's packed FP32 instructions (__ffma2_rn, __fadd2_rn, __fmul2_rn: two
-// single-precision operations per instruction, each rounded exactly like the
-// scalar one), so the node routines below are bit-identical to their scalar
-// form with half as many FP32 arithmetic instructions.
+// FP32 with two rows per lane: the rows go in pairs through GB300's packed
+// FP32 instructions (__ffma2_rn, __fadd2_rn, __fmul2_rn: two single-precision
+// operations per instruction, each rounded exactly like the scalar one), so
+// the node routines below are bit-identical to their scalar form with half as
+// many FP32 arithmetic instructions.  With four rows per lane the scalar form
+// is the faster one (the four-step sweep on 25601 x 128: 20.3 against 22.2 us
+// per step; on 25601 x 64, two rows, the pairs win, 10.3 against 11.0 us), so
+// only K = 2 pairs its rows.
+template <int K>
+constexpr bool kPairRows = (K == 2);
 __device__ __forceinline__ float2 pr2(const float *v, int t) { return make_float2(v[t], v[t + 1]); }
 __device__ __forceinline__ float2 ng2(float2 v) { return make_float2(-v.x, -v.y); }
 __device__ __forceinline__ void st2(float *v, int t, float2 x)
@@ -207,7 +212,7 @@ __device__ __forceinline__ void half_node_q(const T (&a)[4][K], const T (&c)[4][
 {
     const FmaK<T> k1 = fma_k<T>();
     T sR[K], sI[K], upR[K], upI[K], dnR[K], dnI[K];
-    if constexpr (sizeof(T) == 4 && K % 2 == 0) {
+    if constexpr (sizeof(T) == 4 && kPairRows<K>) {
 #pragma unroll
         for (int t = 0; t < K; t += 2) {
             st2(sR, t, __fadd2_rn(pr2(a[0], t), pr2(c[0], t)));
@@ -222,7 +227,7 @@ __device__ __forceinline__ void half_node_q(const T (&a)[4][K], const T (&c)[4][
     }
     theta_neighbours<T, K>(sR, upR, dnR);
     theta_neighbours<T, K>(sI, upI, dnI);
-    if constexpr (sizeof(T) == 4 && K % 2 == 0) {
+    if constexpr (sizeof(T) == 4 && kPairRows<K>) {
 #pragma unroll
         for (int t = 0; t < K; t += 2) {
             const float2 a0 = pr2(a[0], t), a1 = pr2(a[1], t), a2 = pr2(a[2], t), a3 = pr2(a[3], t);
@@ -305,7 +310,7 @@ __device__ __forceinline__ void full_node_q(const T (&hm)[4][K], const T (&hp)[4
 {
     const FmaK<T> k1 = fma_k<T>();
     T sR[K], sI[K], upR[K], upI[K], dnR[K], dnI[K];
-    if constexpr (sizeof(T) == 4 && K % 2 == 0) {
+    if constexpr (sizeof(T) == 4 && kPairRows<K>) {
 #pragma unroll
         for (int t = 0; t < K; t += 2) {
             st2(sR, t, __fadd2_rn(pr2(hp[0], t), pr2(hm[0], t)));
@@ -320,7 +325,7 @@ __device__ __forceinline__ void full_node_q(const T (&hm)[4][K], const T (&hp)[4
     }
     theta_neighbours<T, K>(sR, upR, dnR);
     theta_neighbours<T, K>(sI, upI, dnI);
-    if constexpr (sizeof(T) == 4 && K % 2 == 0) {
+    if constexpr (sizeof(T) == 4 && kPairRows<K>) {
         const float2 e2 = make_float2(e, e);
 #pragma unroll
         for (int t = 0; t < K; t += 2) {
@@ -430,7 +435,7 @@ __device__ __forceinline__ void derive_half(const float *__restrict__ tab, const
     ldk<float, K>(tab + C_FCR * NP, q[H_FCR]);
     ldk<float, K>(tab + C_FCI * NP, q[H_FCI]);
     ldk<float, K>(tab + C_C4H * NP, C4);
-    if constexpr (K % 2 == 0) {
+    if constexpr (kPairRows<K>) {
         const float2 ih = make_float2(fd.ih, fd.ih), t2 = make_float2(fd.t2, fd.t2);
         const float2 m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
@@ -467,7 +472,7 @@ __device__ __forceinline__ void derive_node(const float *__restrict__ tab, const
     ldk<float, K>(tab + (C_FMR - C_B) * NP, q[N_FMR]);
     ldk<float, K>(tab + (C_FMI - C_B) * NP, q[N_FMI]);
     ldk<float, K>(tab + (C_C4N - C_B) * NP, C4);
-    if constexpr (K % 2 == 0) {
+    if constexpr (kPairRows<K>) {
         const float2 bn2 = make_float2(fd.bn2, fd.bn2);
 #pragma unroll
         for (int t = 0; t < K; t += 2) {
