@@ -130,7 +130,8 @@ def test_batch_rejects_mismatched_members():
 def test_full_batched_set_is_bit_identical_to_members_alone():
     """All 24 instances of the batched workload at full size (16x spread in
     size, three theta packings, k = 2, 4, 8) for 12 outer steps, in the
-    launch configuration the benchmark times (autotuned segment, graph)."""
+    launch configuration the benchmark times (the autotuner's choice: for
+    this set the members one after another), and through the work queue."""
     import paper_1010_3816_gb300 as tk
     from inputs import batched_instances
     inst = batched_instances()
@@ -140,10 +141,17 @@ def test_full_batched_set_is_bit_identical_to_members_alone():
     ref = _results(alone)
     for g, _ in alone:
         g.close()
-    batched = [_solver(w) for w in inst]
-    b = tk.Batch([g for g, _ in batched])
-    assert b.info()["kmax"] == 8
-    b.tune(2)
-    b.step(12)
-    _same(_results(batched), ref)
-    b.close()
+    for tuned in (True, False):   # the tuner's choice, then the work queue itself
+        batched = [_solver(w) for w in inst]
+        b = tk.Batch([g for g, _ in batched])
+        assert b.info()["kmax"] == 8
+        if tuned:
+            b.tune(2)
+        else:
+            b.set_segment(12)
+            assert b.info()["seg"] == 12
+        b.step(12)
+        _same(_results(batched), ref)
+        b.close()
+        for g, _ in batched:
+            g.close()

@@ -20,7 +20,7 @@ Their differences from the plain run (kappa) are the run's own conditioning:
 no other correct rounding order can be expected closer.
 
 The GPU runs the workload in the launch configuration the benchmark times
-(graph replay, one block per SM).  Bars: waveforms 1e-12; sampled state per
+(every step of the solve in one persistent launch, one block per SM).  Bars: waveforms 1e-12; sampled state per
 plane and plane norms max(1e-12, 2 kappa), kappa the largest of the five
 runs' differences of that quantity.  Run from the oracle's own coefficient
 tables (tk_set_coefficients), the GPU's difference is its arithmetic's
