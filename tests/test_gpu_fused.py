@@ -166,3 +166,23 @@ def test_persistent_launch_bit_identical(precision, w, calls):
     # and the automatic choice
     s0, w0 = _run(w, precision, 0, calls)
     assert np.array_equal(s0, sp) and all(np.array_equal(a, b) for a, b in zip(w0, wp))
+
+
+# grid sizes around the launch-shape switches (narrow 4-warp blocks below
+# 152 x the wide warp count, one wide block per SM from there), grids that
+# barely give every warp of a narrow launch one column, and uneven splits
+SHAPES = [(64, 32), (607, 32), (1215, 32), (3647, 32), (3648, 32), (3649, 32), (5000, 32),
+          (2431, 64), (2432, 64), (2433, 64), (1215, 128), (1216, 128), (1217, 128), (611, 40)]
+
+
+@pytest.mark.parametrize("Nr,Ntheta", SHAPES, ids=[f"{a}x{b}" for a, b in SHAPES])
+def test_persistent_fp64_dataflow_across_launch_shapes(Nr, Ntheta):
+    """The persistent FP64 sweep (each warp waiting only for the warps it
+    depends on) against one launch per step, bit for bit, on grid sizes
+    around the launch-shape switches."""
+    w = _grid(Nr, Ntheta, substeps=2, observers=((-30.0, 1.5), (-30.0 + (Nr - 1) / 32.0, 1.0)))
+    s1, w1 = _run(w, 0, 1, (5, 2))
+    sp, wp = _run(w, 0, -1, (5, 2))
+    assert np.isfinite(s1).all() and np.abs(s1).max() > 0
+    assert np.array_equal(s1, sp)
+    assert all(np.array_equal(a, b) for a, b in zip(w1, wp))
