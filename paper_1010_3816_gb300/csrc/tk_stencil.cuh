@@ -475,13 +475,12 @@ __device__ __forceinline__ void derive_node(const float *__restrict__ tab, const
 // slot 1 the same at column i0 + 1 times fr; the sample is slot 0 + slot 1.
 // In FP32 a slot holds the four FP32 values Phi_{R,I} at rows j0, j0 + 1, and
 // the read-out forms the same sample from them in FP64 (WaveRead).
-// observe_one: observer k's slot from the column's Phi_R, Phi_I (K rows per
-// lane); all 32 lanes take part, lane 0 writes.
+// observe_one_at: observer k's slot of sample `sample` from the column's
+// Phi_R, Phi_I (K rows per lane); all 32 lanes take part, lane 0 writes.
 template <typename T, int K>
-__device__ __forceinline__ void observe_one(int lane, int k, int slot, const T (&re)[K], const T (&im)[K],
-                                            const ObsDev &obs, double *wave, int64_t cap,
-                                            const long long *sample_ctr, const double *w_row,
-                                            int sample_offset)
+__device__ __forceinline__ void observe_one_at(int lane, int k, int slot, const T (&re)[K], const T (&im)[K],
+                                               const ObsDev &obs, double *wave, int64_t cap,
+                                               const double *w_row, long long sample)
 {
     // only rows j0 and j0 + 1 contribute: fetch them from the lanes that hold
     // them (two shuffles) and let lane 0 do the few operations, instead of a
@@ -506,7 +505,6 @@ __device__ __forceinline__ void observe_one(int lane, int k, int slot, const T (
     br = __shfl_sync(kFull, br, (j0 + 1) / K);
     bi = __shfl_sync(kFull, bi, (j0 + 1) / K);
     if (lane == 0) {
-        const long long sample = *(volatile const long long *)sample_ctr + sample_offset;
         double *dst = wave + ((size_t)k * cap + sample) * 4 + 2 * slot;
         if constexpr (sizeof(T) == 4) {
             // FP32: the values themselves, one 16-byte store, no arithmetic
@@ -524,7 +522,20 @@ __device__ __forceinline__ void observe_one(int lane, int k, int slot, const T (
     }
 }
 
-// Every observer slot at column i.
+// Every observer slot at column i, for sample `sample`.
+template <typename T, int K>
+__device__ __forceinline__ void observe_at(int i, int lane, const T (&re)[K], const T (&im)[K], const ObsDev &obs,
+                                           double *wave, int64_t cap, const double *w_row, long long sample)
+{
+    for (int k = 0; k < obs.n; ++k) {
+        const int slot = (i == obs.i0[k]) ? 0 : ((i == obs.i0[k] + 1) ? 1 : -1);
+        if (slot < 0) continue;
+        observe_one_at<T, K>(lane, k, slot, re, im, obs, wave, cap, w_row, sample);
+    }
+}
+
+// The same with the sample index read from the device counter (which a
+// replayed graph of launches moves on between outer steps) plus an offset.
 template <typename T, int K>
 __device__ __forceinline__ void observe(int i, int lane, const T (&o)[4][K], const ObsDev &obs,
                                         double *wave, int64_t cap, const long long *sample_ctr,
@@ -533,7 +544,9 @@ __device__ __forceinline__ void observe(int i, int lane, const T (&o)[4][K], con
     for (int k = 0; k < obs.n; ++k) {
         const int slot = (i == obs.i0[k]) ? 0 : ((i == obs.i0[k] + 1) ? 1 : -1);
         if (slot < 0) continue;
-        observe_one<T, K>(lane, k, slot, o[0], o[1], obs, wave, cap, sample_ctr, w_row, sample_offset);
+        long long sample = 0;
+        if (lane == 0) sample = *(volatile const long long *)sample_ctr + sample_offset;
+        observe_one_at<T, K>(lane, k, slot, o[0], o[1], obs, wave, cap, w_row, sample);
     }
 }
 

@@ -1009,19 +1009,28 @@ __device__ __forceinline__ void multi_sweep(unsigned char *sh_raw, RingState &rs
                          wscr);
     if (n == 0) return;
     const int row = lane * K;
+    // The sample counter does not move during the launch (advance_sample at
+    // its end): read it once.  All the stored values are loaded before any
+    // sample is formed, so that their loads overlap instead of forming a
+    // chain of round trips through L2 on the warp that sets the launch's pace.
+    const long long base = *(volatile const long long *)wa.sample;
+    T v[kObsCols][LV][2][K];
 #pragma unroll
-    for (int h = 0; h < kObsCols; ++h) {
-        if (oc[h] < 0) continue;
+    for (int h = 0; h < kObsCols; ++h)
 #pragma unroll
         for (int l = 0; l < LV; ++l)
-            if ((mask >> l) & 1) {
+            if (oc[h] >= 0 && ((mask >> l) & 1)) {
                 const T *d = wscr + ((size_t)h * LV + l) * 2 * NP + row;
-                T v[4][K];
-                ldk<T, K>(d, v[0]);
-                ldk<T, K>(d + NP, v[1]);
-                observe<T, K>(oc[h], lane, v, wa.obs, wa.wave, wa.cap, wa.sample, wa.w_row, off[l]);
+                ldk<T, K>(d, v[h][l][0]);
+                ldk<T, K>(d + NP, v[h][l][1]);
             }
-    }
+#pragma unroll
+    for (int h = 0; h < kObsCols; ++h)
+#pragma unroll
+        for (int l = 0; l < LV; ++l)
+            if (oc[h] >= 0 && ((mask >> l) & 1))
+                observe_at<T, K>(oc[h], lane, v[h][l][0], v[h][l][1], wa.obs, wa.wave, wa.cap, wa.w_row,
+                                 base + off[l]);
 }
 
 // Groups of LV steps in one cooperative launch, the blocks waiting for their
