@@ -72,8 +72,8 @@ MEASURED_TRAFFIC = {
     # one persistent launch of 200 steps: 65.775047 + 10.831660 GB, per step
     ("kerr_a0.9_25601x64_38400steps", 0): ((65.775047e9 + 10.831660e9) / 200,
                                            "profiles/lw_persistent_f64_kerr_25601x64.md"),
-    # one launch of 50 sweeps of four steps: 6.683122 + 1.267384 GB
-    ("kerr_a0.9_25601x64_38400steps", 1): ((6.683122e9 + 1.267384e9) / 50,
+    # one launch of 50 sweeps of four steps: 6.726055 + 1.280336 GB
+    ("kerr_a0.9_25601x64_38400steps", 1): ((6.726055e9 + 1.280336e9) / 50,
                                            "profiles/lw_multi_persistent_f32_kerr_25601x64.md"),
 }
 # FP32 on the Kerr workload: every inner step of the solve in one cooperative
